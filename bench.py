@@ -1,0 +1,339 @@
+"""Benchmark: Background SHAP consumer-rows/s on the large workload shaped like the
+paper's KDD-Cup-99 run (3,000,000 consumers x 5,000,000 background rows, 127 features,
+200 ragged depth-6 trees).
+
+One step = the whole hot path on one batch: background decision patterns and counts,
+the pattern-pair contraction and fold (set_background), the consumer patterns, gather
+and accumulation into phi (explain), and the FP64 per-feature global attribution of
+phi.  value = consumer rows / step time, inputs resident in HBM (both larger than L2).
+e2e = the same step through the C ABI with pinned HOST buffers (B and C copied in,
+phi copied out inside the timed region).
+
+--impl reference times the FP64 CPU oracle (the count-regrouped tier) on the host
+cores on a bounded sample of the same workload, extrapolated linearly in the number
+of background rows and consumer rows.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under torchrun,
+one process per GPU, every rank runs its own copy of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "background_shap_consumer_rows_per_sec"
+UNIT = "rows/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, name in enumerate(names):
+                    if r[5 + k].lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_ops(ens) -> dict:
+    """Per consumer row, the work the method must do on the real (unpadded) trees:
+    one compare per inner node and one table lookup-add per (leaf, distinct feature on
+    its path) -- the O(n T L D) term of the paper's complexity table."""
+    compares = adds = 0
+    for t in range(ens.n_trees):
+        o = int(ens.tree_offset[t])
+        stack = [(0, ())]
+        while stack:
+            v, feats = stack.pop()
+            f = int(ens.feature[o + v])
+            if f < 0:
+                adds += len(set(feats))
+            else:
+                compares += 1
+                stack.append((int(ens.left[o + v]), feats + (f,)))
+                stack.append((int(ens.right[o + v]), feats + (f,)))
+    return {"compares": compares, "lookup_adds": adds, "ops": compares + adds}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2511_09376_gb300 as wdf
+    from paper_2511_09376_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.WORKLOADS[args.workload]
+    t_gen = time.time()
+    ens, C, B = synth.make(w)
+    gen_s = time.time() - t_gen
+    n, m, F = C.shape[0], B.shape[0], C.shape[1]
+    ctx = wdf.ctx_create(local_rank)
+    e = wdf.load_ensemble(ctx, ens)
+    info = wdf.ensemble_info(e)
+    dB = torch.from_numpy(B).to(dev)
+    dC = torch.from_numpy(C).to(dev)
+    phi = torch.empty((n, F), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        wdf.set_background(e, dB, args.precision)
+        if ev is not None:
+            ev[0].record(stream)
+        wdf.explain(e, dC, out=phi)
+        if ev is not None:
+            ev[1].record(stream)
+        wdf.global_attribution(ctx, phi)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = wdf.launch_count()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(args.steps):
+        step(kev[k])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = wdf.launch_count() - launches0
+    clk = clocks.stop()
+    ms = start.elapsed_time(stop) / args.steps
+    explain_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI with pinned host buffers
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.from_numpy(C).pin_memory()
+    hphi = torch.empty((n, F), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, min(args.warmup, 2))):
+        wdf.set_background(e, hB, args.precision)
+        wdf.explain(e, hC, out=hphi)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        wdf.set_background(e, hB, args.precision)
+        wdf.explain(e, hC, out=hphi)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    peaks, peak_kind = _peaks()
+    ops = algorithmic_ops(ens)
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # issue roof: 152 SMs x 128 lanes per clock (4 schedulers x 32 lanes)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak_max = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = ops["ops"] * n / (explain_ms * 1e-3) / 1e12
+    hbm_bytes = 2 * n * F * 4
+    result = {
+        "metric": METRIC,
+        "value": world * n / (ms * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": f"{w.name}: n={n} consumers, m={m} background rows, F={F}, T={w.n_trees} trees, depth<={w.depth}",
+            "n_consumers": n, "n_background": m, "n_features": F, "n_trees": w.n_trees, "depth": info["depth"],
+            "precision": args.precision, "live_leaves": info["n_live_leaves"], "signatures": info["n_signatures"],
+            "l2": "inputs larger than L2 (B 2.5 GB, C 1.5 GB)", "parallelism": f"replicas{world}",
+        },
+        "explain_ms": explain_ms,
+        "background_and_reduce_ms": ms - explain_ms,
+        "explain_only_rows_per_s": world * n / (explain_ms * 1e-3),
+        "roofline": {
+            "kernel": "k_explain (consumer patterns + gather + accumulate)",
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": alu_peak_max,
+            "unit": "Top/s",
+            "frac": achieved / alu_peak_max,
+            "traffic": None,
+            "ops_per_row": ops,
+            "peak_basis": f"{sms} SMs x 128 lanes/clk x {peaks.get('sm_max_mhz', 2070.0)} MHz (max SM clock, {peak_kind})",
+            "hbm_gbs": hbm_bytes / (explain_ms * 1e-3) / 1e9,
+            "hbm_frac_of_measured": hbm_bytes / (explain_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+        },
+        "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(B.nbytes + C.nbytes),
+                "d2h_bytes_per_step": int(n * F * 4)},
+        "gpu_launches": int(launches // args.steps),
+        "gpu_launches_timed_region": int(launches),
+        "clocks": clk,
+        "generate_s": gen_s,
+    }
+    return result, ens, C, B
+
+
+def cpu_baseline(ens, C, B, budget_s=20.0):
+    """The FP64 oracle (count-regrouped tier) on a bounded sample; time per background
+    row and per consumer row, extrapolated to the full workload."""
+    import oracle
+    m_s = min(B.shape[0], 100_000)
+    t0 = time.perf_counter()
+    counts = oracle.bg_hist(ens, B[:m_s])
+    t_bg = (time.perf_counter() - t0) / m_s
+    n_s = 64
+    t0 = time.perf_counter()
+    oracle.values_hist(ens, counts, m_s, C[:n_s])
+    t_c = (time.perf_counter() - t0) / n_s
+    total = t_bg * B.shape[0] + t_c * C.shape[0]
+    return {"value": C.shape[0] / total, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"background counts on {m_s} rows ({t_bg * m_s:.2f} s) and values for {n_s} consumers "
+                      f"({t_c * n_s:.2f} s) of the same workload, extrapolated linearly to m={B.shape[0]}, "
+                      f"n={C.shape[0]}: {total:.0f} s for the full workload"}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step is a bounded sample of the workload."""
+    import oracle
+    from paper_2511_09376_gb300 import synth
+    oracle.build()
+    w = synth.WORKLOADS[args.workload]
+    m_s, n_s = 50_000, 32
+    ens, C, B = synth.make(w, n_consumers=n_s, n_background=m_s)
+    n_full, m_full = w.n_consumers, w.n_background
+
+    def step():
+        t0 = time.perf_counter()
+        counts = oracle.bg_hist(ens, B)
+        t1 = time.perf_counter()
+        oracle.values_hist(ens, counts, m_s, C)
+        t2 = time.perf_counter()
+        return (t1 - t0) / m_s * m_full + (t2 - t1) / n_s * n_full
+
+    for _ in range(args.warmup):
+        step()
+    est = [step() for _ in range(args.steps)]
+    full_s = statistics.mean(est)
+    v = n_full / full_s
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": full_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{w.name}: n={n_full} consumers, m={m_full} background rows, F={w.n_features}, "
+                               f"T={w.n_trees} trees, depth<={w.depth}", "parallelism": "host cores"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": f"per step: background counts on {m_s} rows and values for {n_s} consumers, "
+                                   f"extrapolated linearly to m={m_full}, n={n_full}"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, world, rank)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    result, ens, C, B = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            result["cpu_baseline"] = cpu_baseline(ens, C, B)
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

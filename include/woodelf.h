@@ -1,0 +1,154 @@
+/*
+ * woodelf.h -- C ABI of the GB300 (sm_103a) Background-SHAP library.
+ *
+ * The library computes, for a decision-tree ensemble, a background matrix B (m rows)
+ * and consumer rows C (n rows), the Background (interventional) Shapley value of every
+ * feature for every consumer: the Shapley value (Eq. "s") of the game
+ *     v_c(S) = (1/m) sum_{b in B} f(x^S),  x^S_i = c_i if i in S else b_i,
+ * where f is the plain sum of the trees' leaf outputs (section "WOODELF Algorithm":
+ * run per tree and sum).  It follows the paper's WOODELF route (Algorithm 3):
+ *   set_background : per-leaf background decision-pattern counts (Algorithm 1 and
+ *                    Eq. "bg_shap_derivation" step (d)), the Shapley pattern-pair
+ *                    tables (Algorithm 2 with Formula "shap_simplified_formula"), and
+ *                    their contraction s_{l,i} = w_l * M_{l,i} * f_l (step (f));
+ *   explain        : consumer decision patterns, the lookup s_{l,i}[P[l][c]] and the
+ *                    sum over leaves and trees (step (g)).
+ *
+ * Conventions (all entry points):
+ *   - A row goes left at an inner node when x[feature] < threshold (strict float32
+ *     compare; a NaN goes right) -- Def. "decision_tree".
+ *   - Matrices are row-major float32 with a leading dimension (elements) >= the
+ *     feature count.  phi is n x F row-major.
+ *   - Pointers tagged WDF_MEM_DEVICE must be device memory of the context's GPU;
+ *     WDF_MEM_HOST pointers are host memory (pinned memory gives asynchronous copies).
+ *   - Every function returns a wdf_status and never throws; wdf_last_error() gives a
+ *     thread-local message for the last failure on the calling thread.
+ *   - "stream" is a cudaStream_t (NULL = the legacy default stream).  Device work is
+ *     enqueued on it and the call returns without waiting, except where stated.
+ *   - The caller owns every buffer it passes; the library copies what it keeps.
+ */
+#ifndef WOODELF_H
+#define WOODELF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WDF_OK = 0,
+    WDF_EINVAL = 1,        /* malformed argument or call order */
+    WDF_ENOMEM = 2,        /* a device or host allocation failed */
+    WDF_ECUDA = 3,         /* a CUDA runtime call failed */
+    WDF_EUNSUPPORTED = 4,  /* valid input the library does not handle (depth > 8, m == 0) */
+    WDF_ETIMEOUT = 5,
+    WDF_EBUSY = 6
+} wdf_status;
+
+/* Arithmetic of the contraction s = w * M * f (Eq. "bg_shap_derivation" step (f)). */
+typedef enum {
+    WDF_FP32 = 0,    /* FP32 operands, FP32 accumulation (CUDA cores) */
+    WDF_TF32X3 = 1,  /* TF32 hi+lo split operands, three tensor-core products, FP32 accumulation */
+    WDF_BF16X3 = 2   /* BF16 hi+lo split operands, three tensor-core products, FP32 accumulation */
+} wdf_precision;
+
+typedef enum { WDF_MEM_HOST = 0, WDF_MEM_DEVICE = 1 } wdf_memkind;
+
+typedef struct wdf_ctx wdf_ctx;
+typedef struct wdf_ensemble wdf_ensemble;
+
+typedef struct {
+    int32_t n_features;      /* F */
+    int32_t n_trees;         /* T */
+    int32_t depth;           /* D: every tree is laid out as a complete tree of this depth */
+    int32_t n_live_leaves;   /* leaves with a non-zero output after that layout */
+    int32_t n_signatures;    /* distinct repeated-feature patterns of the live paths */
+    int32_t has_background;  /* 1 after a successful wdf_set_background */
+    int64_t device_bytes;    /* device memory the ensemble holds */
+} wdf_info;
+
+/* Context bound to one CUDA device.  Returns WDF_ECUDA if the device is absent. */
+wdf_status wdf_ctx_create(int32_t device, wdf_ctx **out);
+void wdf_ctx_destroy(wdf_ctx *ctx);
+
+/*
+ * Load an ensemble (host arrays, copied).  Trees are stored back to back:
+ * tree_offset[t] is the flat index of tree t's root, tree_offset[n_trees] the node
+ * count.  Per node: feature (-1 for a leaf, else in [0, n_features)), threshold,
+ * left/right child indices local to the tree (-1 for a leaf), value (leaf output).
+ * Definition: Def. "decision_tree" (binary nodes, leaf outputs w_l, strict split).
+ * WDF_EINVAL: offsets not increasing, a child index out of range, a node reached
+ * twice or never, a feature out of range.  WDF_EUNSUPPORTED: a leaf deeper than 8
+ * (patterns are 8-bit, section "Algorithmic Improvements" item 5).  Blocks until the
+ * ensemble is resident on the device.
+ */
+wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, const int64_t *tree_offset,
+                             const int32_t *feature, const float *threshold, const int32_t *left,
+                             const int32_t *right, const float *value, wdf_ensemble **out);
+void wdf_ensemble_destroy(wdf_ensemble *ens);
+wdf_status wdf_ensemble_info(const wdf_ensemble *ens, wdf_info *out);
+
+/*
+ * Set the background B (m x F, leading dimension ldb) and run the consumer-independent
+ * half of Algorithm 3: background pattern counts (step 1), pattern-pair tables (step
+ * 2) and their contraction (step 3), in the given precision.  B is not retained.
+ * WDF_EUNSUPPORTED: m == 0 (an empty background is the path-dependent variant).
+ * Stream-ordered; a later wdf_explain on the same stream sees the result.
+ */
+wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, wdf_memkind kind,
+                              wdf_precision precision, void *stream);
+
+/*
+ * phi[c, i] for the n consumer rows C (leading dimension ldc) into phi (leading
+ * dimension ldphi >= F): Algorithm 3 step 4 / Eq. "bg_shap_derivation" step (g).
+ * C and phi live in the same memory kind.  WDF_EINVAL if no background was set.
+ * Device kind: asynchronous.  Host kind: copies through device staging buffers and
+ * returns once phi is written on the host.
+ */
+wdf_status wdf_explain(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc, wdf_memkind kind,
+                       float *phi, int64_t ldphi, void *stream);
+
+/* E_b f(b), the value of the empty coalition, in FP64 (efficiency property, Appendix
+ * B: sum_i phi_i(c) = f(c) - E_b f(b)).  Waits for the background to be processed. */
+wdf_status wdf_expected_value(const wdf_ensemble *ens, double *out, void *stream);
+
+/*
+ * Global attribution over n explained rows (device pointers): mean_abs[i] =
+ * (1/n) sum_c |phi[c,i]| and mean[i] = (1/n) sum_c phi[c,i], accumulated in FP64 in a
+ * fixed order (the paper's global attribution combines many local attributions,
+ * section "Introduction").  mean_abs and mean are device arrays of F doubles.
+ * Asynchronous.
+ */
+wdf_status wdf_global_attribution(wdf_ctx *ctx, const float *phi, int64_t n, int64_t ldphi, int32_t n_features,
+                                  double *mean_abs, double *mean, void *stream);
+
+/*
+ * Inspection, used by the tests.
+ * wdf_debug_leaf_hist: the background pattern counts vc[l][p_b] (Eq.
+ * "bg_shap_derivation" step (d)) of every leaf of the complete depth-D layout, as
+ * uint32 [T][2^D][2^D] on the host (out_elems must be >= T * 4^D); leaf q of tree t is
+ * the q-th leaf from the left, pattern bits root first.  Synchronous.
+ * wdf_debug_shapley_table: the FP64 pattern-pair table of one path shape, built on the
+ * device (Algorithm 2 + Formula "shap_simplified_formula", unit leaf weight):
+ * out[p_b][k * 2^D + p_c] for path position k, where first[k] is the first path
+ * position holding the same feature as position k (first[k] == k for a new feature);
+ * the value of a feature is stored at its first position, later ones hold 0.  Host
+ * output of 2^D * D * 2^D doubles.  Synchronous.
+ */
+wdf_status wdf_debug_leaf_hist(const wdf_ensemble *ens, uint32_t *out, int64_t out_elems);
+wdf_status wdf_debug_shapley_table(wdf_ctx *ctx, int32_t depth, const int32_t *first, double *out);
+
+/* Number of kernels this library has launched in the process so far (all devices).
+ * Benchmarks read it before and after a timed region. */
+int64_t wdf_launch_count(void);
+
+const char *wdf_last_error(void);
+const char *wdf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WOODELF_H */

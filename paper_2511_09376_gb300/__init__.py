@@ -1,0 +1,28 @@
+"""GB300 (sm_103a) Background SHAP for decision-tree ensembles (WOODELF hot path).
+
+Thin ctypes binding over the C ABI in ``include/woodelf.h``; the names mirror it:
+``ctx_create``, ``load_ensemble``, ``set_background``, ``explain``,
+``expected_value``, ``global_attribution`` and the ``debug_*`` inspectors.  The
+binding only marshals arguments -- every step of the computation runs in the CUDA
+library.  If the library has not been built, importing the binding raises.
+"""
+from ._binding import (  # noqa: F401
+    BF16X3,
+    FP32,
+    TF32X3,
+    Context,
+    Ensemble,
+    WdfError,
+    ctx_create,
+    debug_leaf_hist,
+    debug_shapley_table,
+    ensemble_info,
+    expected_value,
+    explain,
+    global_attribution,
+    launch_count,
+    library_path,
+    load_ensemble,
+    set_background,
+    version,
+)

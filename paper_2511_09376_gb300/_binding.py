@@ -1,0 +1,237 @@
+"""ctypes marshalling for libwoodelf.so (argument conversion only, no arithmetic).
+
+Device tensors are passed by ``data_ptr()`` together with the current torch CUDA
+stream; host inputs may be numpy arrays or CPU tensors (pinned memory makes the
+library's copies asynchronous).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libwoodelf.so")
+
+FP32, TF32X3, BF16X3 = 0, 1, 2
+_PRECISION = {"fp32": FP32, "tf32x3": TF32X3, "bf16x3": BF16X3}
+MEM_HOST, MEM_DEVICE = 0, 1
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        f"{_LIB_PATH} is missing: build the CUDA library first "
+        "(python -c 'import __graft_entry__ as g; g.build()')")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+_c = ctypes
+_vp = _c.c_void_p
+_lib.wdf_last_error.restype = _c.c_char_p
+_lib.wdf_version.restype = _c.c_char_p
+for _name, _args in {
+    "wdf_ctx_create": [_c.c_int32, _c.POINTER(_vp)],
+    "wdf_load_ensemble": [_vp, _c.c_int32, _c.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _c.POINTER(_vp)],
+    "wdf_ensemble_info": [_vp, _vp],
+    "wdf_set_background": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int, _c.c_int, _vp],
+    "wdf_explain": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int, _vp, _c.c_int64, _vp],
+    "wdf_expected_value": [_vp, _c.POINTER(_c.c_double), _vp],
+    "wdf_global_attribution": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int32, _vp, _vp, _vp],
+    "wdf_debug_leaf_hist": [_vp, _vp, _c.c_int64],
+    "wdf_debug_shapley_table": [_vp, _c.c_int32, _vp, _vp],
+}.items():
+    getattr(_lib, _name).argtypes = _args
+    getattr(_lib, _name).restype = _c.c_int
+_lib.wdf_launch_count.argtypes = []
+_lib.wdf_launch_count.restype = _c.c_int64
+_lib.wdf_ctx_destroy.argtypes = [_vp]
+_lib.wdf_ctx_destroy.restype = None
+_lib.wdf_ensemble_destroy.argtypes = [_vp]
+_lib.wdf_ensemble_destroy.restype = None
+
+
+class WdfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"wdf status {status}: {msg}")
+        self.status = status
+
+
+class _Info(_c.Structure):
+    _fields_ = [("n_features", _c.c_int32), ("n_trees", _c.c_int32), ("depth", _c.c_int32),
+                ("n_live_leaves", _c.c_int32), ("n_signatures", _c.c_int32), ("has_background", _c.c_int32),
+                ("device_bytes", _c.c_int64)]
+
+
+def _check(rc):
+    if rc != 0:
+        raise WdfError(rc, _lib.wdf_last_error().decode(errors="replace"))
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process."""
+    return int(_lib.wdf_launch_count())
+
+
+def version() -> str:
+    return _lib.wdf_version().decode()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    if stream is None:
+        torch = _torch()
+        if torch.cuda.is_available():
+            return _vp(torch.cuda.current_stream().cuda_stream)
+        return _vp(0)
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        h = _vp()
+        _check(_lib.wdf_ctx_create(int(device), _c.byref(h)))
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            _lib.wdf_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            _lib.wdf_ensemble_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        return ensemble_info(self)
+
+
+def ctx_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def load_ensemble(ctx: Context, ens) -> Ensemble:
+    """ens: any object with n_features, tree_offset, feature, threshold, left, right, value."""
+    off = _np(ens.tree_offset, np.int64)
+    arrs = [_np(ens.feature, np.int32), _np(ens.threshold, np.float32), _np(ens.left, np.int32),
+            _np(ens.right, np.int32), _np(ens.value, np.float32)]
+    h = _vp()
+    _check(_lib.wdf_load_ensemble(ctx.handle, int(ens.n_features), int(off.shape[0] - 1), off.ctypes.data,
+                                  *[a.ctypes.data for a in arrs], _c.byref(h)))
+    return Ensemble(ctx, h)
+
+
+def ensemble_info(e: Ensemble) -> dict:
+    info = _Info()
+    _check(_lib.wdf_ensemble_info(e.handle, _c.byref(info)))
+    return {k: getattr(info, k) for k, _ in _Info._fields_}
+
+
+def _matrix(x):
+    """(pointer, rows, leading dim, memkind, keepalive) of a row-major float32 matrix."""
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float32 or x.dim() != 2 or x.stride(1) != 1:
+            raise ValueError("expected a 2-D float32 tensor with unit column stride")
+        kind = MEM_DEVICE if x.is_cuda else MEM_HOST
+        return x.data_ptr(), x.shape[0], x.stride(0), kind, x
+    a = np.asarray(x)
+    if a.dtype != np.float32 or a.ndim != 2 or a.strides[1] != 4 or a.strides[0] % 4:
+        a = np.ascontiguousarray(a, dtype=np.float32)
+    return a.ctypes.data, a.shape[0], a.strides[0] // 4, MEM_HOST, a
+
+
+def set_background(e: Ensemble, B, precision="fp32", stream=None) -> None:
+    p, m, ld, kind, keep = _matrix(B)
+    prec = _PRECISION[precision] if isinstance(precision, str) else int(precision)
+    _check(_lib.wdf_set_background(e.handle, _vp(p), int(m), int(ld), kind, prec, _stream_handle(stream)))
+    del keep
+
+
+def explain(e: Ensemble, C, out=None, stream=None):
+    """phi (n x F float32).  Device tensor in -> device tensor out (asynchronous on the
+    stream); host array in -> host array out."""
+    p, n, ld, kind, keep = _matrix(C)
+    F = ensemble_info(e)["n_features"]
+    torch = _torch()
+    if out is None:
+        if kind == MEM_DEVICE:
+            out = torch.empty((n, F), dtype=torch.float32, device=C.device)
+        elif isinstance(C, torch.Tensor):
+            out = torch.empty((n, F), dtype=torch.float32, pin_memory=C.is_pinned())
+        else:
+            out = np.empty((n, F), dtype=np.float32)
+    op, on, old, okind, okeep = _matrix(out)
+    if okind != kind or on != n:
+        raise ValueError("phi must live in the same memory kind as C and have n rows")
+    _check(_lib.wdf_explain(e.handle, _vp(p), int(n), int(ld), kind, _vp(op), int(old), _stream_handle(stream)))
+    del keep, okeep
+    return out
+
+
+def expected_value(e: Ensemble, stream=None) -> float:
+    v = _c.c_double(0.0)
+    _check(_lib.wdf_expected_value(e.handle, _c.byref(v), _stream_handle(stream)))
+    return v.value
+
+
+def global_attribution(ctx: Context, phi, stream=None):
+    """(mean |phi|, mean phi) per feature as FP64 device tensors."""
+    torch = _torch()
+    if not (isinstance(phi, torch.Tensor) and phi.is_cuda and phi.dtype == torch.float32 and phi.stride(1) == 1):
+        raise ValueError("phi must be a float32 CUDA tensor with unit column stride")
+    n, F = phi.shape
+    ma = torch.empty(F, dtype=torch.float64, device=phi.device)
+    mn = torch.empty(F, dtype=torch.float64, device=phi.device)
+    _check(_lib.wdf_global_attribution(ctx.handle, _vp(phi.data_ptr()), int(n), int(phi.stride(0)), int(F),
+                                       _vp(ma.data_ptr()), _vp(mn.data_ptr()), _stream_handle(stream)))
+    return ma, mn
+
+
+def debug_leaf_hist(e: Ensemble) -> np.ndarray:
+    info = ensemble_info(e)
+    T, D = info["n_trees"], info["depth"]
+    out = np.zeros((T, 1 << D, 1 << D), dtype=np.uint32)
+    _check(_lib.wdf_debug_leaf_hist(e.handle, _vp(out.ctypes.data), int(out.size)))
+    return out
+
+
+def debug_shapley_table(ctx: Context, first) -> np.ndarray:
+    f = np.ascontiguousarray(first, dtype=np.int32)
+    D = int(f.shape[0])
+    out = np.zeros((1 << D, D << D), dtype=np.float64)
+    _check(_lib.wdf_debug_shapley_table(ctx.handle, D, _vp(f.ctypes.data), _vp(out.ctypes.data)))
+    return out

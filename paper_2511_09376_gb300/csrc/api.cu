@@ -1,0 +1,407 @@
+// C ABI of the library (declared in include/woodelf.h): context and ensemble
+// lifetime, argument checks, device buffers, and the order of the kernel launches of
+// Algorithm 3.  No kernel here; every step runs in the kernels of k_*.cu.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "wdf_internal.h"
+#include "woodelf.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+wdf_status fail(wdf_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+wdf_status cuda_fail(cudaError_t e, const char *where) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(WDF_ENOMEM, std::string(where) + ": " + cudaGetErrorString(e));
+    }
+    return fail(WDF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define WDF_CUDA(call)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count, int64_t *bytes) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e == cudaSuccess) *bytes += (int64_t)(count * sizeof(T));
+    return e;
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+constexpr int64_t kStageRows = 1 << 18;  // rows per host<->device staging chunk
+
+std::atomic<int64_t> g_launches{0};
+
+}  // namespace
+
+namespace wdf {
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace wdf
+
+struct wdf_ctx {
+    int device = 0;
+    wdf::DevInfo dev;
+};
+
+struct wdf_ensemble {
+    wdf_ctx *ctx = nullptr;
+    wdf::Packed pk;
+    int G = 0, n_live = 0, n_tiles = 0;
+    int64_t bytes = 0;
+    // ensemble (load time)
+    int2 *d_nodes = nullptr;
+    uint64_t *d_live = nullptr;
+    uint32_t *d_keys = nullptr;
+    int32_t *d_group_leaf = nullptr;
+    int32_t *d_leaf_row = nullptr;
+    double *d_w_rows = nullptr;
+    int4 *d_tiles = nullptr;
+    float *d_t32 = nullptr;
+    // background state (set_background)
+    int has_bg = 0;
+    int64_t m = 0;
+    uint32_t *d_hist = nullptr;
+    uint32_t *d_vc = nullptr;
+    float *d_scale = nullptr;
+    float *d_S = nullptr;
+    float *d_sfold = nullptr;
+    double *d_base = nullptr;
+    // staging for host-memory calls
+    float *d_stage_in = nullptr;
+    float *d_stage_out = nullptr;
+};
+
+namespace {
+
+void free_ensemble(wdf_ensemble *e) {
+    dfree(e->d_nodes); dfree(e->d_live); dfree(e->d_keys); dfree(e->d_group_leaf); dfree(e->d_leaf_row);
+    dfree(e->d_w_rows); dfree(e->d_tiles); dfree(e->d_t32);
+    dfree(e->d_hist); dfree(e->d_vc); dfree(e->d_scale); dfree(e->d_S); dfree(e->d_sfold); dfree(e->d_base);
+    dfree(e->d_stage_in); dfree(e->d_stage_out);
+}
+
+wdf_status ensure_staging(wdf_ensemble *e) {
+    if (e->d_stage_in) return WDF_OK;
+    const size_t n = (size_t)kStageRows * e->pk.F;
+    WDF_CUDA(dalloc(&e->d_stage_in, n, &e->bytes));
+    WDF_CUDA(dalloc(&e->d_stage_out, n, &e->bytes));
+    return WDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *wdf_last_error(void) { return g_err.c_str(); }
+
+const char *wdf_version(void) { return "woodelf-gb300 0.1 (sm_103a)"; }
+
+int64_t wdf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+wdf_status wdf_ctx_create(int32_t device, wdf_ctx **out) {
+    if (!out) return fail(WDF_EINVAL, "out is null");
+    *out = nullptr;
+    int count = 0;
+    WDF_CUDA(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return fail(WDF_EINVAL, "device index out of range");
+    DeviceGuard g(device);
+    if (!g.ok) return fail(WDF_ECUDA, "cudaSetDevice failed");
+    wdf_ctx *c = new wdf_ctx();
+    c->device = device;
+    int sms = 0, smem = 0;
+    cudaError_t e1 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e2 = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        delete c;
+        return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaDeviceGetAttribute");
+    }
+    c->dev.sms = sms;
+    c->dev.smem_optin = (size_t)smem;
+    *out = c;
+    return WDF_OK;
+}
+
+void wdf_ctx_destroy(wdf_ctx *ctx) { delete ctx; }
+
+wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, const int64_t *tree_offset,
+                             const int32_t *feature, const float *threshold, const int32_t *left,
+                             const int32_t *right, const float *value, wdf_ensemble **out) {
+    if (!ctx || !out) return fail(WDF_EINVAL, "ctx and out must be non-null");
+    *out = nullptr;
+    wdf_ensemble *e = new wdf_ensemble();
+    e->ctx = ctx;
+    std::string err;
+    const int rc = wdf::pack_ensemble(n_features, n_trees, tree_offset, feature, threshold, left, right, value,
+                                      &e->pk, &err);
+    if (rc != 0) {
+        delete e;
+        return fail((wdf_status)rc, err);
+    }
+    DeviceGuard g(ctx->device);
+    const wdf::Packed &p = e->pk;
+    e->G = (int)p.sig_key.size();
+    e->n_live = (int)p.group_leaf.size();
+    std::vector<int2> nodes((size_t)p.T * p.NI);
+    for (size_t i = 0; i < nodes.size(); ++i) {
+        int32_t bits;
+        std::memcpy(&bits, &p.node_thr[i], 4);
+        nodes[i] = make_int2(p.node_feat[i], bits);
+    }
+    std::vector<double> w_rows((size_t)e->n_live);
+    for (int r = 0; r < e->n_live; ++r) w_rows[(size_t)r] = (double)p.leaf_w[(size_t)p.group_leaf[(size_t)r]];
+    std::vector<int4> tiles;
+    for (int gi = 0; gi < e->G; ++gi)
+        for (int r0 = p.group_off[(size_t)gi]; r0 < p.group_off[(size_t)gi + 1]; r0 += 64)
+            tiles.push_back(make_int4(gi, r0, std::min(r0 + 64, p.group_off[(size_t)gi + 1]), 0));
+    e->n_tiles = (int)tiles.size();
+    const int K = 1 << p.D, N = p.D << p.D;
+    cudaError_t ce = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (ce == cudaSuccess) ce = x; };
+    chk(dalloc(&e->d_nodes, nodes.size(), &e->bytes));
+    chk(dalloc(&e->d_live, p.live.size(), &e->bytes));
+    chk(dalloc(&e->d_keys, p.sig_key.size(), &e->bytes));
+    chk(dalloc(&e->d_group_leaf, p.group_leaf.size(), &e->bytes));
+    chk(dalloc(&e->d_leaf_row, p.leaf_row.size(), &e->bytes));
+    chk(dalloc(&e->d_w_rows, w_rows.size(), &e->bytes));
+    chk(dalloc(&e->d_tiles, tiles.size(), &e->bytes));
+    chk(dalloc(&e->d_t32, (size_t)e->G * K * N, &e->bytes));
+    if (ce == cudaSuccess) {
+        chk(cudaMemcpy(e->d_nodes, nodes.data(), nodes.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(e->d_live, p.live.data(), p.live.size() * 8, cudaMemcpyHostToDevice));
+        if (e->G) chk(cudaMemcpy(e->d_keys, p.sig_key.data(), p.sig_key.size() * 4, cudaMemcpyHostToDevice));
+        if (e->n_live) {
+            chk(cudaMemcpy(e->d_group_leaf, p.group_leaf.data(), p.group_leaf.size() * 4, cudaMemcpyHostToDevice));
+            chk(cudaMemcpy(e->d_w_rows, w_rows.data(), w_rows.size() * 8, cudaMemcpyHostToDevice));
+        }
+        chk(cudaMemcpy(e->d_leaf_row, p.leaf_row.data(), p.leaf_row.size() * 4, cudaMemcpyHostToDevice));
+        if (e->n_tiles) chk(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        // step 2 of Algorithm 3 depends only on the path signatures: build the tables now
+        chk(wdf::launch_tables(p.D, e->d_keys, e->G, e->d_t32, nullptr, 0));
+        chk(cudaStreamSynchronize(0));
+    }
+    if (ce != cudaSuccess) {
+        free_ensemble(e);
+        delete e;
+        return cuda_fail(ce, "wdf_load_ensemble");
+    }
+    *out = e;
+    return WDF_OK;
+}
+
+void wdf_ensemble_destroy(wdf_ensemble *ens) {
+    if (!ens) return;
+    DeviceGuard g(ens->ctx->device);
+    cudaDeviceSynchronize();
+    free_ensemble(ens);
+    delete ens;
+}
+
+wdf_status wdf_ensemble_info(const wdf_ensemble *ens, wdf_info *out) {
+    if (!ens || !out) return fail(WDF_EINVAL, "null argument");
+    out->n_features = ens->pk.F;
+    out->n_trees = ens->pk.T;
+    out->depth = ens->pk.D;
+    out->n_live_leaves = ens->n_live;
+    out->n_signatures = ens->G;
+    out->has_background = ens->has_bg;
+    out->device_bytes = ens->bytes;
+    return WDF_OK;
+}
+
+wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, wdf_memkind kind,
+                              wdf_precision precision, void *stream) {
+    if (!ens) return fail(WDF_EINVAL, "ens is null");
+    if (m == 0) return fail(WDF_EUNSUPPORTED, "empty background (m == 0)");
+    if (m < 0 || !B) return fail(WDF_EINVAL, "m must be positive and B non-null");
+    if (ldb < ens->pk.F) return fail(WDF_EINVAL, "ldb < n_features");
+    if (m > (int64_t)0xFFFFFFFF) return fail(WDF_EUNSUPPORTED, "more than 2^32-1 background rows");
+    if (kind != WDF_MEM_HOST && kind != WDF_MEM_DEVICE) return fail(WDF_EINVAL, "bad memory kind");
+    if (precision != WDF_FP32) return fail(WDF_EUNSUPPORTED, "only WDF_FP32 contraction is available");
+    DeviceGuard g(ens->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const wdf::Packed &p = ens->pk;
+    const int K = 1 << p.D, N = p.D << p.D;
+    const size_t hist_n = (size_t)p.T * p.NS * (2 * K);
+    if (!ens->d_hist) {
+        WDF_CUDA(dalloc(&ens->d_hist, hist_n, &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_vc, (size_t)ens->n_live * K, &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_scale, (size_t)ens->n_live, &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_S, (size_t)ens->n_live * N, &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_sfold, hist_n * wdf::slot_pad(p.D), &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_base, 1, &ens->bytes));
+    }
+    ens->has_bg = 0;
+    WDF_CUDA(cudaMemsetAsync(ens->d_hist, 0, hist_n * 4, st));
+    if (kind == WDF_MEM_DEVICE) {
+        WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, p.F, ens->d_nodes, ens->d_live, p.T, ens->d_hist,
+                                     ens->ctx->dev, st));
+    } else {
+        wdf_status s = ensure_staging(ens);
+        if (s != WDF_OK) return s;
+        for (int64_t r0 = 0; r0 < m; r0 += kStageRows) {
+            const int64_t rows = std::min(kStageRows, m - r0);
+            WDF_CUDA(cudaMemcpy2DAsync(ens->d_stage_in, (size_t)p.F * 4, B + r0 * ldb, (size_t)ldb * 4,
+                                       (size_t)p.F * 4, (size_t)rows, cudaMemcpyHostToDevice, st));
+            WDF_CUDA(wdf::launch_bg_hist(p.D, ens->d_stage_in, rows, p.F, p.F, ens->d_nodes, ens->d_live, p.T,
+                                         ens->d_hist, ens->ctx->dev, st));
+        }
+    }
+    WDF_CUDA(wdf::launch_leaf_counts(p.D, ens->d_hist, ens->d_group_leaf, ens->n_live, ens->d_vc, st));
+    WDF_CUDA(wdf::launch_scale(ens->d_w_rows, ens->n_live, m, ens->d_scale, st));
+    WDF_CUDA(wdf::launch_base_value(p.D, ens->d_vc, ens->d_w_rows, ens->n_live, m, ens->d_base, st));
+    WDF_CUDA(wdf::launch_contract_fp32(p.D, ens->d_vc, ens->d_scale, ens->d_tiles, ens->n_tiles, ens->d_t32,
+                                       ens->d_S, st));
+    WDF_CUDA(wdf::launch_fold(p.D, ens->d_S, ens->d_leaf_row, p.T, ens->d_sfold, st));
+    if (kind == WDF_MEM_HOST) WDF_CUDA(cudaStreamSynchronize(st));
+    ens->m = m;
+    ens->has_bg = 1;
+    return WDF_OK;
+}
+
+wdf_status wdf_explain(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc, wdf_memkind kind, float *phi,
+                       int64_t ldphi, void *stream) {
+    if (!ens) return fail(WDF_EINVAL, "ens is null");
+    if (!ens->has_bg) return fail(WDF_EINVAL, "wdf_set_background must succeed before wdf_explain");
+    if (n < 0) return fail(WDF_EINVAL, "n < 0");
+    if (n == 0) return WDF_OK;
+    if (!C || !phi) return fail(WDF_EINVAL, "C and phi must be non-null");
+    const wdf::Packed &p = ens->pk;
+    if (ldc < p.F || ldphi < p.F) return fail(WDF_EINVAL, "leading dimension < n_features");
+    if (kind != WDF_MEM_HOST && kind != WDF_MEM_DEVICE) return fail(WDF_EINVAL, "bad memory kind");
+    DeviceGuard g(ens->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (kind == WDF_MEM_DEVICE) {
+        WDF_CUDA(wdf::launch_explain(p.D, C, n, ldc, p.F, ens->d_nodes, ens->d_live, ens->d_sfold, p.T, phi, ldphi,
+                                     ens->ctx->dev, st));
+        return WDF_OK;
+    }
+    wdf_status s = ensure_staging(ens);
+    if (s != WDF_OK) return s;
+    for (int64_t r0 = 0; r0 < n; r0 += kStageRows) {
+        const int64_t rows = std::min(kStageRows, n - r0);
+        WDF_CUDA(cudaMemcpy2DAsync(ens->d_stage_in, (size_t)p.F * 4, C + r0 * ldc, (size_t)ldc * 4, (size_t)p.F * 4,
+                                   (size_t)rows, cudaMemcpyHostToDevice, st));
+        WDF_CUDA(wdf::launch_explain(p.D, ens->d_stage_in, rows, p.F, p.F, ens->d_nodes, ens->d_live, ens->d_sfold,
+                                     p.T, ens->d_stage_out, p.F, ens->ctx->dev, st));
+        WDF_CUDA(cudaMemcpy2DAsync(phi + r0 * ldphi, (size_t)ldphi * 4, ens->d_stage_out, (size_t)p.F * 4,
+                                   (size_t)p.F * 4, (size_t)rows, cudaMemcpyDeviceToHost, st));
+    }
+    WDF_CUDA(cudaStreamSynchronize(st));
+    return WDF_OK;
+}
+
+wdf_status wdf_expected_value(const wdf_ensemble *ens, double *out, void *stream) {
+    if (!ens || !out) return fail(WDF_EINVAL, "null argument");
+    if (!ens->has_bg) return fail(WDF_EINVAL, "no background set");
+    DeviceGuard g(ens->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    WDF_CUDA(cudaMemcpyAsync(out, ens->d_base, sizeof(double), cudaMemcpyDeviceToHost, st));
+    WDF_CUDA(cudaStreamSynchronize(st));
+    return WDF_OK;
+}
+
+wdf_status wdf_global_attribution(wdf_ctx *ctx, const float *phi, int64_t n, int64_t ldphi, int32_t n_features,
+                                  double *mean_abs, double *mean, void *stream) {
+    if (!ctx || !mean_abs || !mean) return fail(WDF_EINVAL, "null argument");
+    if (n < 0 || n_features < 1 || ldphi < n_features) return fail(WDF_EINVAL, "bad sizes");
+    if (n > 0 && !phi) return fail(WDF_EINVAL, "phi is null");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t pn = (size_t)wdf::global_attr_blocks(n) * n_features * 2;
+    double *partial = nullptr;
+    WDF_CUDA(cudaMallocAsync((void **)&partial, pn * sizeof(double), st));
+    cudaError_t e = wdf::launch_global_attr(phi, n, ldphi, n_features, partial, mean_abs, mean, st);
+    cudaFreeAsync(partial, st);
+    if (e != cudaSuccess) return cuda_fail(e, "wdf_global_attribution");
+    return WDF_OK;
+}
+
+wdf_status wdf_debug_leaf_hist(const wdf_ensemble *ens, uint32_t *out, int64_t out_elems) {
+    if (!ens || !out) return fail(WDF_EINVAL, "null argument");
+    if (!ens->has_bg) return fail(WDF_EINVAL, "no background set");
+    const wdf::Packed &p = ens->pk;
+    const int64_t total = (int64_t)p.T * p.NL * p.NL;
+    if (out_elems < total) return fail(WDF_EINVAL, "output too small");
+    DeviceGuard g(ens->ctx->device);
+    std::vector<int32_t> all((size_t)p.T * p.NL);
+    for (size_t i = 0; i < all.size(); ++i) all[i] = (int32_t)i;
+    int32_t *d_all = nullptr;
+    uint32_t *d_out = nullptr;
+    int64_t dummy = 0;
+    cudaError_t ce = dalloc(&d_all, all.size(), &dummy);
+    if (ce == cudaSuccess) ce = dalloc(&d_out, (size_t)total, &dummy);
+    if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+    if (ce == cudaSuccess) ce = cudaMemcpy(d_all, all.data(), all.size() * 4, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = wdf::launch_leaf_counts(p.D, ens->d_hist, d_all, (int)all.size(), d_out, 0);
+    if (ce == cudaSuccess) ce = cudaMemcpy(out, d_out, (size_t)total * 4, cudaMemcpyDeviceToHost);
+    dfree(d_all);
+    dfree(d_out);
+    if (ce != cudaSuccess) return cuda_fail(ce, "wdf_debug_leaf_hist");
+    return WDF_OK;
+}
+
+wdf_status wdf_debug_shapley_table(wdf_ctx *ctx, int32_t depth, const int32_t *first, double *out) {
+    if (!ctx || !first || !out) return fail(WDF_EINVAL, "null argument");
+    if (depth < 1 || depth > wdf::kMaxDepth) return fail(WDF_EINVAL, "depth must be in [1, 8]");
+    uint32_t key = 0;
+    for (int k = 0; k < depth; ++k) {
+        if (first[k] < 0 || first[k] > k || first[first[k]] != first[k])
+            return fail(WDF_EINVAL, "first[k] must be the first position of position k's feature");
+        key |= (uint32_t)first[k] << (3 * k);
+    }
+    DeviceGuard g(ctx->device);
+    const size_t K = (size_t)1 << depth, N = (size_t)depth << depth;
+    uint32_t *d_key = nullptr;
+    float *d_t32 = nullptr;
+    double *d_t64 = nullptr;
+    int64_t dummy = 0;
+    cudaError_t ce = dalloc(&d_key, 1, &dummy);
+    if (ce == cudaSuccess) ce = dalloc(&d_t32, K * N, &dummy);
+    if (ce == cudaSuccess) ce = dalloc(&d_t64, K * N, &dummy);
+    if (ce == cudaSuccess) ce = cudaMemcpy(d_key, &key, 4, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = wdf::launch_tables(depth, d_key, 1, d_t32, d_t64, 0);
+    if (ce == cudaSuccess) ce = cudaMemcpy(out, d_t64, K * N * sizeof(double), cudaMemcpyDeviceToHost);
+    dfree(d_key);
+    dfree(d_t32);
+    dfree(d_t64);
+    if (ce != cudaSuccess) return cuda_fail(ce, "wdf_debug_shapley_table");
+    return WDF_OK;
+}
+
+}  // extern "C"

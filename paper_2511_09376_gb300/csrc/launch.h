@@ -1,0 +1,63 @@
+// Kernel launchers (internal).  Every launcher enqueues on the given stream and
+// returns the launch status; none of them allocates.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wdf {
+
+// Counts kernel launches (every launcher adds the kernels it enqueued).
+void count_launches(int k);
+
+struct DevInfo {
+    int sms = 0;
+    size_t smem_optin = 0;  // max dynamic shared memory per block
+};
+
+// Step 1 of Algorithm 3 (background): joint entry counts hist[T][NS][2^(D+1)] (u32,
+// must be zeroed by the caller) of the background rows at every bottom subtree.
+cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, int F, const int2 *nodes,
+                           const uint64_t *live, int T, uint32_t *hist, const DevInfo &dev, cudaStream_t st);
+
+// Per-leaf pattern counts vc[row][p] (u32, 2^D per row) of the live leaves, marginals of
+// the joint entry counts.
+cudaError_t launch_leaf_counts(int D, const uint32_t *hist, const int32_t *group_leaf, int n_live, uint32_t *vc,
+                               cudaStream_t st);
+
+// Step 2: FP64 pattern-pair tables of G path signatures; t32 (and t64 when non-null)
+// laid out [G][2^D][D * 2^D].
+cudaError_t launch_tables(int D, const uint32_t *sig_keys, int G, float *t32, double *t64, cudaStream_t st);
+
+// Split copies of the FP32 tables for the tensor-core contraction: hi + lo with hi
+// rounded to TF32 (bf16 == 0) or BF16 (bf16 == 1); n elements.
+cudaError_t launch_split(const float *src, int64_t n, int bf16, void *hi, void *lo, cudaStream_t st);
+
+// Step 3 on CUDA cores: S[row][k * 2^D + p_c] = scale[row] * sum_p vc[row][p] *
+// T[g][p][k * 2^D + p_c] for every live leaf row of group g.  tiles: (group, row0,
+// row_end, 0) work items of up to 64 rows.
+cudaError_t launch_contract_fp32(int D, const uint32_t *vc, const float *scale, const int4 *tiles, int n_tiles,
+                                 const float *t32, float *S, cudaStream_t st);
+
+// Folds the per-leaf S rows of every bottom subtree into per-entry slot vectors
+// sfold[T][NS][2^(D+1)][SP] (see wdf_internal.h).
+cudaError_t launch_fold(int D, const float *S, const int32_t *leaf_row, int T, float *sfold, cudaStream_t st);
+
+// scale[row] = w[row] / m.
+cudaError_t launch_scale(const double *w, int n_live, int64_t m, float *scale, cudaStream_t st);
+
+// E_b f(b) = (1/m) sum over live leaves of w * vc[all ones] in FP64 (one block).
+cudaError_t launch_base_value(int D, const uint32_t *vc, const double *leaf_w_rows, int n_live, int64_t m,
+                              double *out, cudaStream_t st);
+
+// Step 4: phi of n consumer rows.
+cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, int F, const int2 *nodes,
+                           const uint64_t *live, const float *sfold, int T, float *phi, int64_t ldp,
+                           const DevInfo &dev, cudaStream_t st);
+
+// FP64 column means of |phi| and phi: partial sums per row block, then a fixed-order
+// final sum.  partial holds n_blocks * F * 2 doubles.
+int global_attr_blocks(int64_t n);
+cudaError_t launch_global_attr(const float *phi, int64_t n, int64_t ldp, int F, double *partial,
+                               double *mean_abs, double *mean, cudaStream_t st);
+
+}  // namespace wdf

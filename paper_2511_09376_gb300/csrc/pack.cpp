@@ -1,0 +1,171 @@
+// Host-side validation and complete-layout packing of a tree ensemble.
+//
+// Input format: Def. "decision_tree" (binary inner nodes with feature and threshold,
+// leaves with outputs).  The complete layout and why it changes no value are
+// described in wdf_internal.h.  Leaves are grouped by the path signature of section
+// "Algorithmic Improvements" item 2 (the pattern-pair matrices depend only on the
+// path length and on which features repeat along the path), so each group shares one
+// pattern-pair table.
+#include <algorithm>
+#include <cstring>
+#include <map>
+
+#include "wdf_internal.h"
+
+namespace wdf {
+
+namespace {
+
+struct Src {
+    int F;
+    const int64_t *off;
+    const int32_t *feat;
+    const float *thr;
+    const int32_t *left, *right;
+    const float *val;
+};
+
+// Writes the subtree of input node `node` (local to tree t) at heap position h of
+// depth `depth`; pass-through when node < 0 ("send left") and `keep` says whether the
+// leftmost leaf below keeps output w.
+void place(const Src &s, int t, int32_t node, int h, int depth, float w, bool keep, Packed *p) {
+    const int D = p->D;
+    if (depth == D) {
+        const int q = h - p->NI;
+        p->leaf_w[(size_t)t * p->NL + q] = (node >= 0) ? s.val[s.off[t] + node] : (keep ? w : 0.0f);
+        return;
+    }
+    const size_t k = (size_t)t * p->NI + h;
+    if (node >= 0 && s.feat[s.off[t] + node] >= 0) {
+        const int64_t g = s.off[t] + node;
+        p->node_feat[k] = s.feat[g];
+        p->node_thr[k] = s.thr[g];
+        place(s, t, s.left[g], 2 * h + 1, depth + 1, 0.0f, false, p);
+        place(s, t, s.right[g], 2 * h + 2, depth + 1, 0.0f, false, p);
+        return;
+    }
+    // an input leaf above depth D, or a node under a pass-through: route every row left
+    float wl = w;
+    bool kl = keep;
+    if (node >= 0) {  // input leaf: its output moves to the leftmost leaf below
+        wl = s.val[s.off[t] + node];
+        kl = true;
+    }
+    p->node_feat[k] = p->F;  // virtual column, always 0
+    p->node_thr[k] = 1.0f;   // 0 < 1: left
+    place(s, t, -1, 2 * h + 1, depth + 1, wl, kl, p);
+    place(s, t, -1, 2 * h + 2, depth + 1, 0.0f, false, p);
+}
+
+}  // namespace
+
+int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const float *thr, const int32_t *left,
+                  const int32_t *right, const float *val, Packed *out, std::string *err) {
+    if (F < 1 || T < 1 || !off || !feat || !thr || !left || !right || !val) {
+        *err = "n_features and n_trees must be >= 1 and all arrays non-null";
+        return 1;
+    }
+    if (off[0] != 0) {
+        *err = "tree_offset[0] must be 0";
+        return 1;
+    }
+    int max_depth = 0;
+    std::vector<int> depth_of, seen;
+    for (int t = 0; t < T; ++t) {
+        const int64_t o = off[t], sz = off[t + 1] - off[t];
+        if (sz < 1 || sz > (1 << 20)) {
+            *err = "tree " + std::to_string(t) + ": node count must be in [1, 2^20]";
+            return 1;
+        }
+        depth_of.assign((size_t)sz, -1);
+        seen.assign((size_t)sz, 0);
+        std::vector<int32_t> queue;
+        queue.push_back(0);
+        depth_of[0] = 0;
+        seen[0] = 1;
+        size_t head = 0;
+        while (head < queue.size()) {
+            const int32_t v = queue[head++];
+            const int64_t g = o + v;
+            if (feat[g] < 0) {
+                max_depth = std::max(max_depth, depth_of[(size_t)v]);
+                continue;
+            }
+            if (feat[g] >= F) {
+                *err = "tree " + std::to_string(t) + " node " + std::to_string(v) + ": feature out of range";
+                return 1;
+            }
+            for (int32_t c : {left[g], right[g]}) {
+                if (c <= 0 || c >= sz) {
+                    *err = "tree " + std::to_string(t) + " node " + std::to_string(v) + ": child index out of range";
+                    return 1;
+                }
+                if (seen[(size_t)c]) {
+                    *err = "tree " + std::to_string(t) + " node " + std::to_string(c) + ": reached twice";
+                    return 1;
+                }
+                seen[(size_t)c] = 1;
+                depth_of[(size_t)c] = depth_of[(size_t)v] + 1;
+                if (depth_of[(size_t)c] > kMaxDepth) {
+                    *err = "tree " + std::to_string(t) + ": depth above 8 is not supported";
+                    return 4;
+                }
+                queue.push_back(c);
+            }
+        }
+        if ((int64_t)queue.size() != sz) {
+            *err = "tree " + std::to_string(t) + ": " + std::to_string(sz - (int64_t)queue.size()) +
+                   " node(s) not reachable from the root";
+            return 1;
+        }
+    }
+    Packed &p = *out;
+    p = Packed();
+    p.F = F;
+    p.T = T;
+    p.D = std::max(kMinDepth, max_depth);
+    p.NI = (1 << p.D) - 1;
+    p.NL = 1 << p.D;
+    p.NS = 1 << (p.D - 2);
+    p.node_feat.assign((size_t)T * p.NI, 0);
+    p.node_thr.assign((size_t)T * p.NI, 0.0f);
+    p.leaf_w.assign((size_t)T * p.NL, 0.0f);
+    p.live.assign((size_t)T, 0);
+    p.leaf_row.assign((size_t)T * p.NL, -1);
+    Src s{F, off, feat, thr, left, right, val};
+    for (int t = 0; t < T; ++t) place(s, t, 0, 0, 0, 0.0f, false, &p);
+
+    // live bottom subtrees and signature groups of the live leaves
+    std::map<uint32_t, std::vector<int32_t>> groups;
+    const int D = p.D;
+    for (int t = 0; t < T; ++t) {
+        for (int q = 0; q < p.NL; ++q) {
+            if (p.leaf_w[(size_t)t * p.NL + q] == 0.0f) continue;
+            p.live[(size_t)t] |= (uint64_t)1 << (q >> 2);
+            int32_t pf[kMaxDepth];
+            uint32_t key = 0;
+            for (int k = 0; k < D; ++k) {
+                const int h = ((p.NL + q) >> (D - k)) - 1;  // heap index of the depth-k node on the path
+                const int32_t f = p.node_feat[(size_t)t * p.NI + h];
+                pf[k] = (f == F) ? -(k + 1) : f;  // pass-through positions never repeat
+                int first = k;
+                for (int j = 0; j < k; ++j)
+                    if (pf[j] == pf[k]) { first = j; break; }
+                key |= (uint32_t)first << (3 * k);
+            }
+            groups[key].push_back(t * p.NL + q);
+        }
+    }
+    p.group_off.push_back(0);
+    for (auto &kv : groups) {
+        p.sig_key.push_back(kv.first);
+        for (int32_t leaf : kv.second) {
+            p.leaf_row[(size_t)leaf] = (int32_t)p.group_leaf.size();
+            p.group_leaf.push_back(leaf);
+        }
+        p.group_off.push_back((int32_t)p.group_leaf.size());
+    }
+    return 0;
+}
+
+}  // namespace wdf

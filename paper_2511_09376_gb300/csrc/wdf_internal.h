@@ -1,0 +1,49 @@
+// Internal declarations of the GB300 Background-SHAP library (not part of the ABI).
+//
+// Layout used by every kernel ("complete layout"): each tree is re-laid out as a
+// complete binary tree of the ensemble's depth D (2 <= D <= 8) in heap order -- inner
+// node v has children 2v+1 (left) and 2v+2 (right); leaf q (0-based from the left) is
+// heap position NI + q.  A leaf of the input at depth d < D is pushed down to depth D
+// through "pass-through" nodes that send every row left (they test a virtual feature
+// column F that is always 0 against threshold 1); the pushed-down leaf keeps the
+// output, the other leaves below a pass-through node get output 0.  This changes no
+// value: on a pass-through node both the consumer and the baseline follow the path to
+// the kept leaf, which is rule 3 of the cube construction (no literal), and leaves
+// of output 0 add nothing.
+//
+// "Bottom subtree" s (0 <= s < NS = 2^(D-2)) is the complete subtree of height 2 rooted
+// at heap node r = NS - 1 + s: three inner nodes r, 2r+1, 2r+2 and four leaves 4s..4s+3.
+// Everything consumer-side is indexed by the "entry" of a row at a bottom subtree:
+//   e = (pp << 3) | (d_r << 2) | (d_{2r+1} << 1) | d_{2r+2},
+// pp = the row's decision pattern at r (D-2 bits, root first), d_v = split at node v.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace wdf {
+
+constexpr int kMaxDepth = 8;
+constexpr int kMinDepth = 2;
+
+struct Packed {
+    int F = 0, T = 0, D = 0;
+    int NI = 0, NL = 0, NS = 0;
+    std::vector<int32_t> node_feat;   // [T][NI]  F for pass-through nodes
+    std::vector<float> node_thr;      // [T][NI]
+    std::vector<float> leaf_w;        // [T][NL]
+    std::vector<uint64_t> live;       // [T] bit s: bottom subtree s has a non-zero leaf
+    // live leaves grouped by path signature (first-occurrence positions)
+    std::vector<uint32_t> sig_key;    // [G] 3 bits per path position
+    std::vector<int32_t> group_off;   // [G+1]
+    std::vector<int32_t> group_leaf;  // [n_live] t * NL + q, grouped
+    std::vector<int32_t> leaf_row;    // [T][NL] row of the leaf in group_leaf, -1 if not live
+};
+
+// Validates and lays out an ensemble; returns a wdf_status value and fills err.
+int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const float *thr, const int32_t *left,
+                  const int32_t *right, const float *val, Packed *out, std::string *err);
+
+inline int slot_pad(int D) { return (D + 1) <= 4 ? 4 : ((D + 1) <= 8 ? 8 : 12); }
+
+}  // namespace wdf

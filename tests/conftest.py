@@ -7,6 +7,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# Both native libraries are built before any test imports them (a no-op when the
+# sources are unchanged); nvcc cross-compiles without a GPU.
+import __graft_entry__  # noqa: E402
+
+__graft_entry__._load_build_module().build()
+import oracle  # noqa: E402
+
+oracle.build()
+
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built CUDA library")
