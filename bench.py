@@ -91,6 +91,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def profiled_traffic(summary: str, sources: list, units: int):
+    """DRAM bytes per launch from a committed ncu summary (per-unit figure x units), or
+    None when the kernel sources changed since the counters were taken."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and not line.startswith("|"))
+    h = hashlib.sha256()
+    for p in sources:
+        with open(os.path.join(ROOT, "paper_2511_09376_gb300", "csrc", p), "rb") as f:
+            h.update(f.read())
+    if fields.get("source_sha256_16", "").strip() != h.hexdigest()[:16]:
+        return None
+    return float(fields["traffic_bytes_per_unit"]) * units
+
+
 def algorithmic_ops(ens) -> dict:
     """Per consumer row, the work the method must do on the real (unpadded) trees:
     one compare per inner node and one table lookup-add per (leaf, distinct feature on
@@ -231,7 +249,8 @@ def run_ours(args, rank, world, local_rank):
             "peak": alu_peak_max,
             "unit": "Top/s",
             "frac": achieved / alu_peak_max,
-            "traffic": None,
+            "traffic": profiled_traffic("k_explain_large.md", ["k_explain.cu", "wdf_device.cuh"], n),
+            "algorithmic_bytes": hbm_bytes,
             "ops_per_row": ops,
             "peak_basis": f"{sms} SMs x 128 lanes/clk x {peaks.get('sm_max_mhz', 2070.0)} MHz (max SM clock, {peak_kind})",
             "hbm_gbs": hbm_bytes / (explain_ms * 1e-3) / 1e9,

@@ -64,7 +64,7 @@ void dfree(T *&p) {
     p = nullptr;
 }
 
-constexpr int64_t kStageRows = 1 << 18;  // rows per host<->device staging chunk
+constexpr int64_t kStageRows = 1 << 19;  // rows per host<->device staging chunk
 
 std::atomic<int64_t> g_launches{0};
 
@@ -93,6 +93,14 @@ struct wdf_ensemble {
     double *d_w_rows = nullptr;
     int4 *d_tiles = nullptr;
     float *d_t32 = nullptr;
+    int32_t *d_rn_key = nullptr;
+    float *d_rn_thr = nullptr;
+    int32_t *d_rn_count = nullptr;
+    uint64_t *d_pt_mask = nullptr;
+    float *d_zero = nullptr;  // 64 zero bytes: the entry a dead bottom subtree reads
+    wdf::TreeArrays arrays() const {
+        return wdf::TreeArrays{d_nodes, d_rn_key, d_rn_thr, d_rn_count, d_pt_mask, d_live};
+    }
     // background state (set_background)
     int has_bg = 0;
     int64_t m = 0;
@@ -102,9 +110,12 @@ struct wdf_ensemble {
     float *d_S = nullptr;
     float *d_sfold = nullptr;
     double *d_base = nullptr;
-    // staging for host-memory calls
-    float *d_stage_in = nullptr;
-    float *d_stage_out = nullptr;
+    // staging for host-memory calls: two buffers per direction, one per internal stream
+    float *d_stage_in[2] = {nullptr, nullptr};
+    float *d_stage_out[2] = {nullptr, nullptr};
+    int64_t stage_rows = 0;
+    cudaStream_t ist[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -112,16 +123,55 @@ namespace {
 void free_ensemble(wdf_ensemble *e) {
     dfree(e->d_nodes); dfree(e->d_live); dfree(e->d_keys); dfree(e->d_group_leaf); dfree(e->d_leaf_row);
     dfree(e->d_w_rows); dfree(e->d_tiles); dfree(e->d_t32);
+    dfree(e->d_rn_key); dfree(e->d_rn_thr); dfree(e->d_rn_count); dfree(e->d_pt_mask); dfree(e->d_zero);
     dfree(e->d_hist); dfree(e->d_vc); dfree(e->d_scale); dfree(e->d_S); dfree(e->d_sfold); dfree(e->d_base);
-    dfree(e->d_stage_in); dfree(e->d_stage_out);
+    for (int i = 0; i < 2; ++i) {
+        dfree(e->d_stage_in[i]);
+        dfree(e->d_stage_out[i]);
+        if (e->ist[i]) cudaStreamDestroy(e->ist[i]);
+        if (e->ev_join[i]) cudaEventDestroy(e->ev_join[i]);
+        e->ist[i] = nullptr;
+        e->ev_join[i] = nullptr;
+    }
+    if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+    e->ev_fork = nullptr;
 }
 
-wdf_status ensure_staging(wdf_ensemble *e) {
-    if (e->d_stage_in) return WDF_OK;
-    const size_t n = (size_t)kStageRows * e->pk.F;
-    WDF_CUDA(dalloc(&e->d_stage_in, n, &e->bytes));
-    WDF_CUDA(dalloc(&e->d_stage_out, n, &e->bytes));
+// Double-buffered staging for host-memory calls: chunk i of the rows goes through
+// buffer i % 2 on internal stream i % 2, so the copy engines of one chunk overlap the
+// kernels of the other.  Grows to the largest chunk seen (at most kStageRows rows).
+wdf_status ensure_staging(wdf_ensemble *e, int64_t rows, bool out) {
+    rows = std::min(rows, kStageRows);
+    if (!e->ist[0]) {
+        for (int i = 0; i < 2; ++i) {
+            WDF_CUDA(cudaStreamCreateWithFlags(&e->ist[i], cudaStreamNonBlocking));
+            WDF_CUDA(cudaEventCreateWithFlags(&e->ev_join[i], cudaEventDisableTiming));
+        }
+        WDF_CUDA(cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming));
+    }
+    if (rows > e->stage_rows) {
+        WDF_CUDA(cudaDeviceSynchronize());
+        for (int i = 0; i < 2; ++i) {
+            dfree(e->d_stage_in[i]);
+            dfree(e->d_stage_out[i]);
+        }
+        e->stage_rows = 0;
+        const size_t n = (size_t)rows * e->pk.F;
+        for (int i = 0; i < 2; ++i) {
+            WDF_CUDA(dalloc(&e->d_stage_in[i], n, &e->bytes));
+            WDF_CUDA(dalloc(&e->d_stage_out[i], n, &e->bytes));
+        }
+        e->stage_rows = rows;
+    }
+    (void)out;
     return WDF_OK;
+}
+
+// Copy `rows` rows of F floats between a strided host matrix and a packed device one.
+cudaError_t copy_rows(float *dst, int64_t ldd, const float *src, int64_t lds, int64_t rows, int F,
+                      cudaMemcpyKind kind, cudaStream_t st) {
+    if (ldd == F && lds == F) return cudaMemcpyAsync(dst, src, (size_t)rows * F * 4, kind, st);
+    return cudaMemcpy2DAsync(dst, (size_t)ldd * 4, src, (size_t)lds * 4, (size_t)F * 4, (size_t)rows, kind, st);
 }
 
 }  // namespace
@@ -201,6 +251,11 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
     chk(dalloc(&e->d_w_rows, w_rows.size(), &e->bytes));
     chk(dalloc(&e->d_tiles, tiles.size(), &e->bytes));
     chk(dalloc(&e->d_t32, (size_t)e->G * K * N, &e->bytes));
+    chk(dalloc(&e->d_rn_key, p.rn_key.size(), &e->bytes));
+    chk(dalloc(&e->d_rn_thr, p.rn_thr.size(), &e->bytes));
+    chk(dalloc(&e->d_rn_count, p.rn_count.size(), &e->bytes));
+    chk(dalloc(&e->d_pt_mask, p.pt_mask.size(), &e->bytes));
+    chk(dalloc(&e->d_zero, 16, &e->bytes));
     if (ce == cudaSuccess) {
         chk(cudaMemcpy(e->d_nodes, nodes.data(), nodes.size() * sizeof(int2), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(e->d_live, p.live.data(), p.live.size() * 8, cudaMemcpyHostToDevice));
@@ -210,6 +265,11 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
             chk(cudaMemcpy(e->d_w_rows, w_rows.data(), w_rows.size() * 8, cudaMemcpyHostToDevice));
         }
         chk(cudaMemcpy(e->d_leaf_row, p.leaf_row.data(), p.leaf_row.size() * 4, cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(e->d_rn_key, p.rn_key.data(), p.rn_key.size() * 4, cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(e->d_rn_thr, p.rn_thr.data(), p.rn_thr.size() * 4, cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(e->d_rn_count, p.rn_count.data(), p.rn_count.size() * 4, cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(e->d_pt_mask, p.pt_mask.data(), p.pt_mask.size() * 8, cudaMemcpyHostToDevice));
+        chk(cudaMemset(e->d_zero, 0, 16 * sizeof(float)));
         if (e->n_tiles) chk(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
         // step 2 of Algorithm 3 depends only on the path signatures: build the tables now
         chk(wdf::launch_tables(p.D, e->d_keys, e->G, e->d_t32, nullptr, 0));
@@ -269,17 +329,24 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
     ens->has_bg = 0;
     WDF_CUDA(cudaMemsetAsync(ens->d_hist, 0, hist_n * 4, st));
     if (kind == WDF_MEM_DEVICE) {
-        WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, p.F, ens->d_nodes, ens->d_live, p.T, ens->d_hist,
-                                     ens->ctx->dev, st));
+        WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, p.F, ens->arrays(), p.T, ens->d_hist, ens->ctx->dev, st));
     } else {
-        wdf_status s = ensure_staging(ens);
+        wdf_status s = ensure_staging(ens, m, false);
         if (s != WDF_OK) return s;
-        for (int64_t r0 = 0; r0 < m; r0 += kStageRows) {
-            const int64_t rows = std::min(kStageRows, m - r0);
-            WDF_CUDA(cudaMemcpy2DAsync(ens->d_stage_in, (size_t)p.F * 4, B + r0 * ldb, (size_t)ldb * 4,
-                                       (size_t)p.F * 4, (size_t)rows, cudaMemcpyHostToDevice, st));
-            WDF_CUDA(wdf::launch_bg_hist(p.D, ens->d_stage_in, rows, p.F, p.F, ens->d_nodes, ens->d_live, p.T,
-                                         ens->d_hist, ens->ctx->dev, st));
+        WDF_CUDA(cudaEventRecord(ens->ev_fork, st));
+        for (int i = 0; i < 2; ++i) WDF_CUDA(cudaStreamWaitEvent(ens->ist[i], ens->ev_fork, 0));
+        int64_t chunk = 0;
+        for (int64_t r0 = 0; r0 < m; r0 += ens->stage_rows, ++chunk) {
+            const int64_t rows = std::min(ens->stage_rows, m - r0);
+            const int b = (int)(chunk & 1);
+            WDF_CUDA(copy_rows(ens->d_stage_in[b], p.F, B + r0 * ldb, ldb, rows, p.F, cudaMemcpyHostToDevice,
+                               ens->ist[b]));
+            WDF_CUDA(wdf::launch_bg_hist(p.D, ens->d_stage_in[b], rows, p.F, p.F, ens->arrays(), p.T, ens->d_hist,
+                                         ens->ctx->dev, ens->ist[b]));
+        }
+        for (int i = 0; i < 2; ++i) {
+            WDF_CUDA(cudaEventRecord(ens->ev_join[i], ens->ist[i]));
+            WDF_CUDA(cudaStreamWaitEvent(st, ens->ev_join[i], 0));
         }
     }
     WDF_CUDA(wdf::launch_leaf_counts(p.D, ens->d_hist, ens->d_group_leaf, ens->n_live, ens->d_vc, st));
@@ -307,20 +374,27 @@ wdf_status wdf_explain(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc
     DeviceGuard g(ens->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (kind == WDF_MEM_DEVICE) {
-        WDF_CUDA(wdf::launch_explain(p.D, C, n, ldc, p.F, ens->d_nodes, ens->d_live, ens->d_sfold, p.T, phi, ldphi,
+        WDF_CUDA(wdf::launch_explain(p.D, C, n, ldc, p.F, ens->arrays(), ens->d_sfold, ens->d_zero, p.T, phi, ldphi,
                                      ens->ctx->dev, st));
         return WDF_OK;
     }
-    wdf_status s = ensure_staging(ens);
+    wdf_status s = ensure_staging(ens, n, true);
     if (s != WDF_OK) return s;
-    for (int64_t r0 = 0; r0 < n; r0 += kStageRows) {
-        const int64_t rows = std::min(kStageRows, n - r0);
-        WDF_CUDA(cudaMemcpy2DAsync(ens->d_stage_in, (size_t)p.F * 4, C + r0 * ldc, (size_t)ldc * 4, (size_t)p.F * 4,
-                                   (size_t)rows, cudaMemcpyHostToDevice, st));
-        WDF_CUDA(wdf::launch_explain(p.D, ens->d_stage_in, rows, p.F, p.F, ens->d_nodes, ens->d_live, ens->d_sfold,
-                                     p.T, ens->d_stage_out, p.F, ens->ctx->dev, st));
-        WDF_CUDA(cudaMemcpy2DAsync(phi + r0 * ldphi, (size_t)ldphi * 4, ens->d_stage_out, (size_t)p.F * 4,
-                                   (size_t)p.F * 4, (size_t)rows, cudaMemcpyDeviceToHost, st));
+    WDF_CUDA(cudaEventRecord(ens->ev_fork, st));
+    for (int i = 0; i < 2; ++i) WDF_CUDA(cudaStreamWaitEvent(ens->ist[i], ens->ev_fork, 0));
+    int64_t chunk = 0;
+    for (int64_t r0 = 0; r0 < n; r0 += ens->stage_rows, ++chunk) {
+        const int64_t rows = std::min(ens->stage_rows, n - r0);
+        const int b = (int)(chunk & 1);
+        cudaStream_t sb = ens->ist[b];
+        WDF_CUDA(copy_rows(ens->d_stage_in[b], p.F, C + r0 * ldc, ldc, rows, p.F, cudaMemcpyHostToDevice, sb));
+        WDF_CUDA(wdf::launch_explain(p.D, ens->d_stage_in[b], rows, p.F, p.F, ens->arrays(), ens->d_sfold,
+                                     ens->d_zero, p.T, ens->d_stage_out[b], p.F, ens->ctx->dev, sb));
+        WDF_CUDA(copy_rows(phi + r0 * ldphi, ldphi, ens->d_stage_out[b], p.F, rows, p.F, cudaMemcpyDeviceToHost, sb));
+    }
+    for (int i = 0; i < 2; ++i) {
+        WDF_CUDA(cudaEventRecord(ens->ev_join[i], ens->ist[i]));
+        WDF_CUDA(cudaStreamWaitEvent(st, ens->ev_join[i], 0));
     }
     WDF_CUDA(cudaStreamSynchronize(st));
     return WDF_OK;

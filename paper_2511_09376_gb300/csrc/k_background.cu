@@ -8,115 +8,183 @@
 // four leaf patterns of the subtree are functions of e, so per-leaf counts are exact
 // marginals of these joint counts (the sibling-leaf observation of section
 // "Algorithmic Improvements" item 3, applied two levels up).
+//
+// Work split: the trees are cut into chunks whose counters fit in shared memory as
+// 16-bit halves of 32-bit words; blocks are numbered chunk-fastest, so the blocks that
+// stage the same row tile run at the same time and share it through L2.  A block
+// flushes its 16-bit counters into the global 32-bit counts before any can overflow.
 #include <algorithm>
+#include <cstdlib>
 
 #include "launch.h"
 #include "wdf_device.cuh"
 
 namespace wdf {
 
-template <int D, int RT>
+// Shared memory layout (bytes, 16-aligned pieces): x tile | tree metadata | real-node
+// lists | 16-bit counters.
+template <int D>
+struct BgLayout {
+    size_t x, meta, rn, hist, total;
+    static __host__ __device__ size_t up(size_t v) { return (v + 15) & ~(size_t)15; }
+    __host__ __device__ BgLayout(int F, int RT, int G, bool smem_hist) {
+        x = up((size_t)(F + 1) * (RT + 1) * 4);
+        meta = up((size_t)G * sizeof(TreeMeta));
+        rn = up((size_t)G * Shape<D>::NI * sizeof(int2));
+        hist = smem_hist ? up((size_t)G * Shape<D>::NS * Shape<D>::E * 2) : 0;
+        total = x + meta + rn + hist;
+    }
+};
+
+template <int D, int RT, bool SMEM, bool AGG>
 __global__ void __launch_bounds__(RT) k_bg_hist(const float *__restrict__ B, int64_t m, int64_t ldb, int F,
-                                                const int2 *__restrict__ nodes, const uint64_t *__restrict__ live,
-                                                int T, int G, int use_smem, uint32_t *__restrict__ hist) {
+                                                TreeArrays ta, int T, int G, int chunks,
+                                                uint32_t *__restrict__ hist) {
     using S = Shape<D>;
     constexpr int XS = RT + 1;
-    extern __shared__ __align__(16) uint32_t smem[];
-    float *sx = reinterpret_cast<float *>(smem);
-    uint32_t *sh = smem + (size_t)(F + 1) * XS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const BgLayout<D> L(F, RT, G, SMEM);
+    float *sx = reinterpret_cast<float *>(smem_raw);
+    TreeMeta *smeta = reinterpret_cast<TreeMeta *>(smem_raw + L.x);
+    int2 *srn = reinterpret_cast<int2 *>(smem_raw + L.x + L.meta);
+    uint32_t *sh = reinterpret_cast<uint32_t *>(smem_raw + L.x + L.meta + L.rn);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int t0 = blockIdx.y * G;
+    const int chunk = blockIdx.x % chunks;
+    const int slice = blockIdx.x / chunks, nslices = gridDim.x / chunks;
+    const int t0 = chunk * G;
     const int g_cnt = min(G, T - t0);
-    const int chunk_bins = g_cnt * S::NS * S::E;
-    uint32_t *hdst = use_smem ? sh : hist + (size_t)t0 * S::NS * S::E;
-    if (use_smem)
-        for (int i = tid; i < chunk_bins; i += RT) sh[i] = 0u;
-    for (int64_t row0 = (int64_t)blockIdx.x * RT; row0 < m; row0 += (int64_t)gridDim.x * RT) {
+    const int bins = g_cnt * S::NS * S::E;  // 16-bit counters, two per word
+    uint32_t *gdst = hist + (size_t)t0 * S::NS * S::E;
+    stage_trees<D>(t0, g_cnt, XS, ta.nodes, ta.rn_key, ta.rn_thr, ta.rn_count, ta.pt_mask, ta.live, srn, nullptr,
+                   smeta, tid, RT);
+    if (SMEM)
+        for (int i = tid; i < bins / 2; i += RT) sh[i] = 0u;
+    int64_t since_flush = 0;
+    for (int64_t row0 = (int64_t)slice * RT; row0 < m; row0 += (int64_t)nslices * RT) {
         __syncthreads();
+        if (SMEM && since_flush + RT > 65535) {  // a 16-bit counter could overflow: flush
+            for (int i = tid; i < bins / 2; i += RT) {
+                const uint32_t v = sh[i];
+                if (v & 0xFFFFu) atomicAdd(gdst + 2 * i, v & 0xFFFFu);
+                if (v >> 16) atomicAdd(gdst + 2 * i + 1, v >> 16);
+                sh[i] = 0u;
+            }
+            since_flush = 0;
+        }
         for (int r = warp; r < RT; r += RT / 32) {
             const int64_t row = row0 + r;
             const float *src = B + row * ldb;
             for (int f = lane; f < F; f += 32) sx[f * XS + r] = (row < m) ? __ldg(src + f) : 0.0f;
         }
-        if (tid < RT) sx[F * XS + tid] = 0.0f;
+        sx[F * XS + tid] = 0.0f;
         __syncthreads();
+        since_flush += RT;
         const bool valid = row0 + tid < m;
         for (int g = 0; g < g_cnt; ++g) {
-            const int t = t0 + g;
-            uint32_t dm[S::NW];
-            tree_decisions<D>(nodes + (size_t)t * S::NI, sx, XS, tid, dm);
+            const TreeMeta &mt = smeta[g];
+            uint64_t dm[S::NW];
+            tree_decisions<D>(srn + (size_t)g * S::NI, mt, sx, tid, dm);
             uint32_t ent[S::NS];
             subtree_entries<D>(dm, ent);
-            const uint64_t lv = __ldg(live + t);
+            const uint64_t lv = mt.live;
 #pragma unroll
             for (int s = 0; s < S::NS; ++s) {
-                if ((lv >> s) & 1ull) {
-                    if (valid) atomicAdd(hdst + ((size_t)g * S::NS + s) * S::E + ent[s], 1u);
+                if ((lv >> s) & 1ull) {  // warp-uniform
+                    const uint32_t idx = (uint32_t)(g * S::NS + s) * S::E + ent[s];
+                    if (AGG) {
+                        // lanes with the same counter add once, by the lowest such lane
+                        const uint32_t key = valid ? idx : 0xFFFFFFFFu;
+                        const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+                        if (valid && lane == __ffs(peers) - 1) {
+                            const uint32_t k = (uint32_t)__popc(peers);
+                            if (SMEM)
+                                atomicAdd(sh + (idx >> 1), k << ((idx & 1u) << 4));
+                            else
+                                atomicAdd(gdst + idx, k);
+                        }
+                    } else if (valid) {
+                        if (SMEM)
+                            atomicAdd(sh + (idx >> 1), 1u << ((idx & 1u) << 4));
+                        else
+                            atomicAdd(gdst + idx, 1u);
+                    }
                 }
             }
         }
     }
-    if (use_smem) {
+    if (SMEM) {
         __syncthreads();
-        uint32_t *dst = hist + (size_t)t0 * S::NS * S::E;
-        for (int i = tid; i < chunk_bins; i += RT) {
+        for (int i = tid; i < bins / 2; i += RT) {
             const uint32_t v = sh[i];
-            if (v) atomicAdd(dst + i, v);
+            if (v & 0xFFFFu) atomicAdd(gdst + 2 * i, v & 0xFFFFu);
+            if (v >> 16) atomicAdd(gdst + 2 * i + 1, v >> 16);
         }
     }
 }
 
-template <int D, int RT>
-static cudaError_t bg_hist_t(const float *B, int64_t m, int64_t ldb, int F, const int2 *nodes, const uint64_t *live,
-                             int T, uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
-    using S = Shape<D>;
-    const size_t xbytes = (size_t)(F + 1) * (RT + 1) * sizeof(float);
-    const size_t tbytes = (size_t)S::NS * S::E * sizeof(uint32_t);
-    const size_t budget = dev.smem_optin;
-    int G = 0;
-    if (xbytes < budget) G = (int)std::min<size_t>((size_t)T, (budget - xbytes) / tbytes);
-    const int use_smem = G >= 1;
-    if (!use_smem) G = T;  // counts go straight to global memory
-    const size_t smem = xbytes + (use_smem ? (size_t)G * tbytes : 0);
-    if (smem > budget) return cudaErrorInvalidConfiguration;
-    auto kern = k_bg_hist<D, RT>;
+template <int D, int RT, bool SMEM, bool AGG>
+static cudaError_t bg_hist_launch(const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T, int G,
+                                  size_t smem, const DevInfo &dev, uint32_t *hist, cudaStream_t st) {
+    auto kern = k_bg_hist<D, RT, SMEM, AGG>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    const int chunks = (T + G - 1) / G;
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RT, smem);
     if (err != cudaSuccess) return err;
     per_sm = std::max(per_sm, 1);
+    const int chunks = (T + G - 1) / G;
     const int64_t tiles = (m + RT - 1) / RT;
-    const int64_t want = std::max<int64_t>(1, ((int64_t)dev.sms * per_sm * 2 + chunks - 1) / chunks);
-    dim3 grid((unsigned)std::min<int64_t>(tiles, want), (unsigned)chunks);
-    kern<<<grid, RT, smem, st>>>(B, m, ldb, F, nodes, live, T, G, use_smem, hist);
+    const int64_t slices = std::max<int64_t>(1, std::min<int64_t>(tiles, ((int64_t)dev.sms * per_sm) / chunks));
+    kern<<<(unsigned)(slices * chunks), RT, smem, st>>>(B, m, ldb, F, ta, T, G, chunks, hist);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int D>
-static cudaError_t bg_hist_d(const float *B, int64_t m, int64_t ldb, int F, const int2 *nodes, const uint64_t *live,
-                             int T, uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
-    // 128 rows per block while a row tile and one tree's counts fit, else smaller tiles
-    const size_t tbytes = (size_t)Shape<D>::NS * Shape<D>::E * sizeof(uint32_t);
-    if ((size_t)(F + 1) * 129 * 4 + tbytes <= dev.smem_optin)
-        return bg_hist_t<D, 128>(B, m, ldb, F, nodes, live, T, hist, dev, st);
-    if ((size_t)(F + 1) * 65 * 4 + tbytes <= dev.smem_optin)
-        return bg_hist_t<D, 64>(B, m, ldb, F, nodes, live, T, hist, dev, st);
-    return bg_hist_t<D, 32>(B, m, ldb, F, nodes, live, T, hist, dev, st);
+template <int D, int RT>
+static cudaError_t bg_hist_t(const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T,
+                             uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
+    // resident blocks per SM to aim for (shared memory is split between them)
+    int bps = 1;
+    if (const char *env = std::getenv("WDF_BG_BLOCKS_PER_SM")) bps = std::max(1, std::atoi(env));
+    bool agg = false;
+    if (const char *env = std::getenv("WDF_BG_AGG")) agg = std::atoi(env) != 0;
+    const size_t budget = std::min(dev.smem_optin, (size_t)(228 * 1024) / bps - 1024);
+    int G = std::min(T, 256);
+    while (G > 1 && BgLayout<D>(F, RT, G, true).total > budget) --G;
+    const bool smem_hist = BgLayout<D>(F, RT, G, true).total <= budget;
+    if (!smem_hist) {  // counters straight to global memory
+        G = std::min(T, 64);
+        while (G > 1 && BgLayout<D>(F, RT, G, false).total > dev.smem_optin) --G;
+    }
+    const size_t smem = BgLayout<D>(F, RT, G, smem_hist).total;
+    if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
+    if (smem_hist)
+        return agg ? bg_hist_launch<D, RT, true, true>(B, m, ldb, F, ta, T, G, smem, dev, hist, st)
+                   : bg_hist_launch<D, RT, true, false>(B, m, ldb, F, ta, T, G, smem, dev, hist, st);
+    return agg ? bg_hist_launch<D, RT, false, true>(B, m, ldb, F, ta, T, G, smem, dev, hist, st)
+               : bg_hist_launch<D, RT, false, false>(B, m, ldb, F, ta, T, G, smem, dev, hist, st);
 }
 
-cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, int F, const int2 *nodes,
-                           const uint64_t *live, int T, uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
+template <int D>
+static cudaError_t bg_hist_d(const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T,
+                             uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
+    // 128 rows per block while a row tile fits comfortably, else smaller tiles
+    if ((size_t)(F + 1) * 129 * 4 <= dev.smem_optin / 3) return bg_hist_t<D, 128>(B, m, ldb, F, ta, T, hist, dev, st);
+    if ((size_t)(F + 1) * 65 * 4 <= dev.smem_optin / 3) return bg_hist_t<D, 64>(B, m, ldb, F, ta, T, hist, dev, st);
+    return bg_hist_t<D, 32>(B, m, ldb, F, ta, T, hist, dev, st);
+}
+
+cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T,
+                           uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
     switch (D) {
-        case 2: return bg_hist_d<2>(B, m, ldb, F, nodes, live, T, hist, dev, st);
-        case 3: return bg_hist_d<3>(B, m, ldb, F, nodes, live, T, hist, dev, st);
-        case 4: return bg_hist_d<4>(B, m, ldb, F, nodes, live, T, hist, dev, st);
-        case 5: return bg_hist_d<5>(B, m, ldb, F, nodes, live, T, hist, dev, st);
-        case 6: return bg_hist_d<6>(B, m, ldb, F, nodes, live, T, hist, dev, st);
-        case 7: return bg_hist_d<7>(B, m, ldb, F, nodes, live, T, hist, dev, st);
-        case 8: return bg_hist_d<8>(B, m, ldb, F, nodes, live, T, hist, dev, st);
+        case 2: return bg_hist_d<2>(B, m, ldb, F, ta, T, hist, dev, st);
+        case 3: return bg_hist_d<3>(B, m, ldb, F, ta, T, hist, dev, st);
+        case 4: return bg_hist_d<4>(B, m, ldb, F, ta, T, hist, dev, st);
+        case 5: return bg_hist_d<5>(B, m, ldb, F, ta, T, hist, dev, st);
+        case 6: return bg_hist_d<6>(B, m, ldb, F, ta, T, hist, dev, st);
+        case 7: return bg_hist_d<7>(B, m, ldb, F, ta, T, hist, dev, st);
+        case 8: return bg_hist_d<8>(B, m, ldb, F, ta, T, hist, dev, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -127,13 +195,12 @@ cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, int F,
 __global__ void k_leaf_counts(int D, const uint32_t *__restrict__ hist, const int32_t *__restrict__ group_leaf,
                               int n_live, uint32_t *__restrict__ vc) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int NLb = D;  // log2 leaves per tree
     const int64_t total = (int64_t)n_live << D;
     if (idx >= total) return;
     const int row = (int)(idx >> D);
     const uint32_t p = (uint32_t)(idx & ((1 << D) - 1));
     const int leaf = __ldg(group_leaf + row);
-    const int t = leaf >> NLb, q = leaf & ((1 << D) - 1);
+    const int t = leaf >> D, q = leaf & ((1 << D) - 1);
     const int s = q >> 2, j = q & 3;
     const int NS = 1 << (D - 2), E = 1 << (D + 1);
     const uint32_t pp = p >> 2, fn = (p >> 1) & 1u, fc = p & 1u;
@@ -184,10 +251,6 @@ cudaError_t launch_base_value(int D, const uint32_t *vc, const double *leaf_w_ro
     count_launches(1);
     return cudaGetLastError();
 }
-
-}  // namespace wdf
-
-namespace wdf {
 
 // scale[row] = w_row / m, the leaf weight and the 1/|B| of Eq. "bg_shap_derivation"
 // step (e) folded into one FP32 factor per leaf.

@@ -2,32 +2,79 @@
 // phi[c, i] = sum over trees and leaves of s_{l,i}[P[l][c]].
 //
 // One thread per consumer row.  The block stages its rows feature-major in shared
-// memory together with a per-row phi accumulator of the same shape.  Per tree the
-// thread evaluates the inner nodes (decision bitmask in registers), forms its entry at
-// every live bottom subtree, and gathers one slot vector per subtree from the folded
-// table: the slots of the subtree's three inner nodes go straight into phi[feature of
-// the node]; the slots of the nodes above accumulate in registers (one per node, the
-// node-level form of the NumPy indexing of section "Algorithmic Improvements" item 6)
-// and are added into phi once per tree.  The order of every floating-point addition
-// into a row's phi depends only on the ensemble, never on which rows share a block.
+// memory together with a per-row phi accumulator of the same shape, and the real
+// inner nodes of a chunk of trees.  Per tree the thread evaluates those nodes
+// (decision bitmask in registers), forms its entry at every bottom subtree, and
+// gathers one slot vector per subtree from the folded table -- all gathers of a tree
+// are issued before any is used, so their L2 latency overlaps; a dead subtree reads a
+// zero row instead.  The slots of the subtree's three inner nodes go straight into
+// phi[feature of the node]; the slots of the nodes above accumulate in registers (one
+// per node, the node-level form of the NumPy indexing of section "Algorithmic
+// Improvements" item 6) and are added into phi once per tree.  Pass-through nodes
+// carry nothing and are skipped.  The order of every floating-point addition into a
+// row's phi depends only on the ensemble, never on which rows share a block.
 #include <algorithm>
+#include <cstdlib>
 
 #include "launch.h"
 #include "wdf_device.cuh"
 
 namespace wdf {
 
+template <int D>
+struct ExplainCfg {
+    static constexpr int TCH = 8;  // trees per shared-memory chunk
+    static constexpr int GS = (Shape<D>::NS * Shape<D>::SP <= 128) ? Shape<D>::NS : (64 / Shape<D>::SP);
+};
+
+template <int D>
+struct ExLayout {
+    size_t x, meta, rn, fo, f3, total;
+    static __host__ __device__ size_t up(size_t v) { return (v + 15) & ~(size_t)15; }
+    __host__ __device__ ExLayout(int F, int TC) {
+        x = up((size_t)(F + 1) * (TC + 1) * 4);  // one of x and phi
+        meta = up((size_t)ExplainCfg<D>::TCH * sizeof(TreeMeta));
+        rn = up((size_t)ExplainCfg<D>::TCH * Shape<D>::NI * sizeof(int2));
+        fo = up((size_t)ExplainCfg<D>::TCH * Shape<D>::NI * sizeof(int));
+        f3 = up((size_t)ExplainCfg<D>::TCH * Shape<D>::NS * sizeof(int4));
+        total = 2 * x + meta + rn + fo + f3;
+    }
+};
+
+__device__ __forceinline__ float4 ldg_f4(const float4 *p) {
+    float4 r;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+// One 32-byte entry in a single 256-bit load (the address is 32-byte aligned).
+__device__ __forceinline__ void ldg_f8(const float4 *p, float4 &a, float4 &b) {
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
 template <int D, int TC>
 __global__ void __launch_bounds__(TC) k_explain(const float *__restrict__ C, int64_t n, int64_t ldc, int F,
-                                                const int2 *__restrict__ nodes, const uint64_t *__restrict__ live,
-                                                const float *__restrict__ sfold, int T, float *__restrict__ phi,
+                                                TreeArrays ta, const float *__restrict__ sfold,
+                                                const float *__restrict__ zero, int T, float *__restrict__ phi,
                                                 int64_t ldp) {
     using S = Shape<D>;
+    using X = ExplainCfg<D>;
     constexpr int XS = TC + 1;
     constexpr int NA = S::NS > 1 ? S::NS - 1 : 1;
-    extern __shared__ __align__(16) float smem[];
-    float *sx = smem;
-    float *sp = smem + (size_t)(F + 1) * XS;
+    constexpr int GS = X::GS;
+    constexpr int Q = S::SP / 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const ExLayout<D> L(F, TC);
+    float *sx = reinterpret_cast<float *>(smem_raw);
+    float *sp = reinterpret_cast<float *>(smem_raw + L.x);
+    TreeMeta *smeta = reinterpret_cast<TreeMeta *>(smem_raw + 2 * L.x);
+    int2 *srn = reinterpret_cast<int2 *>(smem_raw + 2 * L.x + L.meta);
+    int *sfo = reinterpret_cast<int *>(smem_raw + 2 * L.x + L.meta + L.rn);
+    int *sf3 = reinterpret_cast<int *>(smem_raw + 2 * L.x + L.meta + L.rn + L.fo);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t c0 = (int64_t)blockIdx.x * TC;
     for (int r = warp; r < TC; r += TC / 32) {
@@ -37,40 +84,68 @@ __global__ void __launch_bounds__(TC) k_explain(const float *__restrict__ C, int
     }
     for (int i = tid; i < (F + 1) * XS; i += TC) sp[i] = 0.0f;
     sx[F * XS + tid] = 0.0f;
-    __syncthreads();
     float *myphi = sp + tid;
-    for (int t = 0; t < T; ++t) {
-        const int2 *tn = nodes + (size_t)t * S::NI;
-        uint32_t dm[S::NW];
-        tree_decisions<D>(tn, sx, XS, tid, dm);
-        uint32_t ent[S::NS];
-        subtree_entries<D>(dm, ent);
-        const uint64_t lv = __ldg(live + t);
-        const float *tf = sfold + (size_t)t * S::NS * S::E * S::SP;
-        float acc[NA];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
-#pragma unroll
-        for (int s = 0; s < S::NS; ++s) {
-            if ((lv >> s) & 1ull) {
-                const float4 *src = reinterpret_cast<const float4 *>(tf + ((size_t)s * S::E + ent[s]) * S::SP);
-                float v[S::SP];
-#pragma unroll
-                for (int k = 0; k < S::SP / 4; ++k) {
-                    const float4 q = __ldg(src + k);
-                    v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
-                }
-                const int r = S::NS - 1 + s;
-#pragma unroll
-                for (int k = 0; k < D - 2; ++k) acc[((r + 1) >> (D - 2 - k)) - 1] += v[k];
-                myphi[__ldg(&tn[r].x) * XS] += v[D - 2];
-                myphi[__ldg(&tn[2 * r + 1].x) * XS] += v[D - 1];
-                myphi[__ldg(&tn[2 * r + 2].x) * XS] += v[D];
-            }
+    const float4 *z4 = reinterpret_cast<const float4 *>(zero);
+    for (int tc0 = 0; tc0 < T; tc0 += X::TCH) {
+        const int tcn = min(X::TCH, T - tc0);
+        __syncthreads();
+        stage_trees<D>(tc0, tcn, XS, ta.nodes, ta.rn_key, ta.rn_thr, ta.rn_count, ta.pt_mask, ta.live, srn, sfo,
+                       smeta, tid, TC);
+        __syncthreads();
+        // phi offsets of the three inner nodes of every bottom subtree, one 128-bit word each
+        for (int i = tid; i < tcn * S::NS; i += TC) {
+            const int g = i / S::NS, r = S::NS - 1 + (i % S::NS);
+            const int *fo = sfo + g * S::NI;
+            reinterpret_cast<int4 *>(sf3)[i] = make_int4(fo[r], fo[2 * r + 1], fo[2 * r + 2], 0);
         }
-        if (S::NS > 1) {
+        __syncthreads();
+        for (int g = 0; g < tcn; ++g) {
+            const int t = tc0 + g;
+            const TreeMeta &mt = smeta[g];
+            const int *fo = sfo + g * S::NI;
+            const int4 *fs3 = reinterpret_cast<const int4 *>(sf3 + (size_t)g * S::NS * 4);
+            uint64_t dm[S::NW];
+            tree_decisions<D>(srn + g * S::NI, mt, sx, tid, dm);
+            uint32_t ent[S::NS];
+            subtree_entries<D>(dm, ent);
+            const uint64_t lv = mt.live;
+            const float4 *tf = reinterpret_cast<const float4 *>(sfold + (size_t)t * S::NS * S::E * S::SP);
+            float acc[NA];
 #pragma unroll
-            for (int a = 0; a < S::NS - 1; ++a) myphi[__ldg(&tn[a].x) * XS] += acc[a];
+            for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
+#pragma unroll
+            for (int s0 = 0; s0 < S::NS; s0 += GS) {
+                const uint64_t gmask = (GS >= 64) ? ~0ull : (((1ull << GS) - 1ull) << s0);
+                if (!(lv & gmask)) continue;  // every subtree of the group is dead (warp-uniform)
+                float4 v[GS][Q];
+#pragma unroll
+                for (int j = 0; j < GS; ++j) {
+                    const bool lj = (lv >> (s0 + j)) & 1ull;
+                    const float4 *src = lj ? tf + ((size_t)(s0 + j) * S::E + ent[s0 + j]) * Q : z4;
+                    if (Q == 2) {
+                        ldg_f8(src, v[j][0], v[j][Q > 1 ? 1 : 0]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < Q; ++k) v[j][k] = ldg_f4(src + k);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < GS; ++j) {
+                    const int r = S::NS - 1 + s0 + j;
+                    const float *vj = reinterpret_cast<const float *>(&v[j][0]);
+#pragma unroll
+                    for (int k = 0; k < D - 2; ++k) acc[((r + 1) >> (D - 2 - k)) - 1] += vj[k];
+                    // pass-through nodes add into the scratch row, dead subtrees add zeros
+                    const int4 f3 = fs3[s0 + j];
+                    myphi[f3.x] += vj[D - 2];
+                    myphi[f3.y] += vj[D - 1];
+                    myphi[f3.z] += vj[D];
+                }
+            }
+            if (S::NS > 1) {
+#pragma unroll
+                for (int a = 0; a < S::NS - 1; ++a) myphi[fo[a]] += acc[a];
+            }
         }
     }
     __syncthreads();
@@ -83,39 +158,39 @@ __global__ void __launch_bounds__(TC) k_explain(const float *__restrict__ C, int
 }
 
 template <int D, int TC>
-static cudaError_t explain_t(const float *C, int64_t n, int64_t ldc, int F, const int2 *nodes, const uint64_t *live,
-                             const float *sfold, int T, float *phi, int64_t ldp, const DevInfo &dev, cudaStream_t st) {
-    const size_t smem = 2 * (size_t)(F + 1) * (TC + 1) * sizeof(float);
+static cudaError_t explain_t(const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, const float *sfold,
+                             const float *zero, int T, float *phi, int64_t ldp, const DevInfo &dev, cudaStream_t st) {
+    const size_t smem = ExLayout<D>(F, TC).total;
     if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
     auto kern = k_explain<D, TC>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     const int64_t blocks = (n + TC - 1) / TC;
-    kern<<<(unsigned)blocks, TC, smem, st>>>(C, n, ldc, F, nodes, live, sfold, T, phi, ldp);
+    kern<<<(unsigned)blocks, TC, smem, st>>>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int D>
-static cudaError_t explain_d(const float *C, int64_t n, int64_t ldc, int F, const int2 *nodes, const uint64_t *live,
-                             const float *sfold, int T, float *phi, int64_t ldp, const DevInfo &dev, cudaStream_t st) {
-    if (2 * (size_t)(F + 1) * 65 * 4 <= dev.smem_optin / 2)
-        return explain_t<D, 64>(C, n, ldc, F, nodes, live, sfold, T, phi, ldp, dev, st);
-    return explain_t<D, 32>(C, n, ldc, F, nodes, live, sfold, T, phi, ldp, dev, st);
+static cudaError_t explain_d(const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, const float *sfold,
+                             const float *zero, int T, float *phi, int64_t ldp, const DevInfo &dev, cudaStream_t st) {
+    if (ExLayout<D>(F, 64).total <= dev.smem_optin / 2)
+        return explain_t<D, 64>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
+    return explain_t<D, 32>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
 }
 
-cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, int F, const int2 *nodes,
-                           const uint64_t *live, const float *sfold, int T, float *phi, int64_t ldp,
+cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta,
+                           const float *sfold, const float *zero, int T, float *phi, int64_t ldp,
                            const DevInfo &dev, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     switch (D) {
-        case 2: return explain_d<2>(C, n, ldc, F, nodes, live, sfold, T, phi, ldp, dev, st);
-        case 3: return explain_d<3>(C, n, ldc, F, nodes, live, sfold, T, phi, ldp, dev, st);
-        case 4: return explain_d<4>(C, n, ldc, F, nodes, live, sfold, T, phi, ldp, dev, st);
-        case 5: return explain_d<5>(C, n, ldc, F, nodes, live, sfold, T, phi, ldp, dev, st);
-        case 6: return explain_d<6>(C, n, ldc, F, nodes, live, sfold, T, phi, ldp, dev, st);
-        case 7: return explain_d<7>(C, n, ldc, F, nodes, live, sfold, T, phi, ldp, dev, st);
-        case 8: return explain_d<8>(C, n, ldc, F, nodes, live, sfold, T, phi, ldp, dev, st);
+        case 2: return explain_d<2>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
+        case 3: return explain_d<3>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
+        case 4: return explain_d<4>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
+        case 5: return explain_d<5>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
+        case 6: return explain_d<6>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
+        case 7: return explain_d<7>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
+        case 8: return explain_d<8>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
         default: return cudaErrorInvalidValue;
     }
 }

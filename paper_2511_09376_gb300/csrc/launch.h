@@ -9,6 +9,16 @@ namespace wdf {
 // Counts kernel launches (every launcher adds the kernels it enqueued).
 void count_launches(int k);
 
+// Device arrays describing the complete layout of an ensemble (see wdf_internal.h).
+struct TreeArrays {
+    const int2 *nodes;        // [T][NI] (feature, threshold bits); feature F = pass-through
+    const int32_t *rn_key;    // [T][NI] compacted real inner nodes: heap | feature << 8
+    const float *rn_thr;      // [T][NI]
+    const int32_t *rn_count;  // [T]
+    const uint64_t *pt_mask;  // [T][4]
+    const uint64_t *live;     // [T]
+};
+
 struct DevInfo {
     int sms = 0;
     size_t smem_optin = 0;  // max dynamic shared memory per block
@@ -16,8 +26,8 @@ struct DevInfo {
 
 // Step 1 of Algorithm 3 (background): joint entry counts hist[T][NS][2^(D+1)] (u32,
 // must be zeroed by the caller) of the background rows at every bottom subtree.
-cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, int F, const int2 *nodes,
-                           const uint64_t *live, int T, uint32_t *hist, const DevInfo &dev, cudaStream_t st);
+cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T,
+                           uint32_t *hist, const DevInfo &dev, cudaStream_t st);
 
 // Per-leaf pattern counts vc[row][p] (u32, 2^D per row) of the live leaves, marginals of
 // the joint entry counts.
@@ -49,9 +59,9 @@ cudaError_t launch_scale(const double *w, int n_live, int64_t m, float *scale, c
 cudaError_t launch_base_value(int D, const uint32_t *vc, const double *leaf_w_rows, int n_live, int64_t m,
                               double *out, cudaStream_t st);
 
-// Step 4: phi of n consumer rows.
-cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, int F, const int2 *nodes,
-                           const uint64_t *live, const float *sfold, int T, float *phi, int64_t ldp,
+// Step 4: phi of n consumer rows.  zero: 64 bytes of zeros (the entry of a dead subtree).
+cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta,
+                           const float *sfold, const float *zero, int T, float *phi, int64_t ldp,
                            const DevInfo &dev, cudaStream_t st);
 
 // FP64 column means of |phi| and phi: partial sums per row block, then a fixed-order

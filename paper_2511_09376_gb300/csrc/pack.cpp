@@ -135,6 +135,26 @@ int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const f
     Src s{F, off, feat, thr, left, right, val};
     for (int t = 0; t < T; ++t) place(s, t, 0, 0, 0, 0.0f, false, &p);
 
+    // compact lists of the inner nodes that test a real feature
+    p.rn_count.assign((size_t)T, 0);
+    p.rn_key.assign((size_t)T * p.NI, 0);
+    p.rn_thr.assign((size_t)T * p.NI, 0.0f);
+    p.pt_mask.assign((size_t)T * 4, 0);
+    for (int t = 0; t < T; ++t) {
+        int c = 0;
+        for (int v = 0; v < p.NI; ++v) {
+            const size_t k = (size_t)t * p.NI + v;
+            if (p.node_feat[k] == F) {
+                p.pt_mask[(size_t)t * 4 + (v >> 6)] |= (uint64_t)1 << (v & 63);
+            } else {
+                p.rn_key[(size_t)t * p.NI + c] = v | (p.node_feat[k] << 8);
+                p.rn_thr[(size_t)t * p.NI + c] = p.node_thr[k];
+                ++c;
+            }
+        }
+        p.rn_count[(size_t)t] = c;
+    }
+
     // live bottom subtrees and signature groups of the live leaves
     std::map<uint32_t, std::vector<int32_t>> groups;
     const int D = p.D;

@@ -33,6 +33,12 @@ struct Packed {
     std::vector<float> node_thr;      // [T][NI]
     std::vector<float> leaf_w;        // [T][NL]
     std::vector<uint64_t> live;       // [T] bit s: bottom subtree s has a non-zero leaf
+    // per tree, the inner nodes that test a real feature, compacted: (heap | feature << 8,
+    // threshold bits), rn_count of them; the other inner nodes are pass-through nodes
+    std::vector<int32_t> rn_count;    // [T]
+    std::vector<int32_t> rn_key;      // [T][NI]
+    std::vector<float> rn_thr;        // [T][NI]
+    std::vector<uint64_t> pt_mask;    // [T][4] bit v: inner node v is a pass-through node
     // live leaves grouped by path signature (first-occurrence positions)
     std::vector<uint32_t> sig_key;    // [G] 3 bits per path position
     std::vector<int32_t> group_off;   // [G+1]
