@@ -125,6 +125,25 @@ wdf_status wdf_global_attribution(wdf_ctx *ctx, const float *phi, int64_t n, int
                                   double *mean_abs, double *mean, void *stream);
 
 /*
+ * wdf_global_attribution without any device allocation.  The paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory when they need the
+ * reduction -- code running under a framework whose caching allocator already holds the
+ * GPU's memory (a raw cudaMalloc there can fail), or latency-critical loops where an
+ * allocation or free may block the host or synchronise the device.
+ * Same arguments and the same result (same kernels, same summation order) as
+ * wdf_global_attribution, with the device index in place of a context.  The FP64
+ * partial sums live in a fixed 2 MiB array of device memory inside the library (held on
+ * every GPU that loads the library until the process exits); WDF_EINVAL when
+ * ceil(n / 4096) * n_features * 2 exceeds its 262,144 doubles (for 127 features: up to
+ * about 4.2 million rows).  Calls share that array and it keeps the last call's
+ * contents: calls that overlap on the GPU race and must be ordered (e.g. one stream).
+ * The first call on a device looks up the array's address with that device current;
+ * make it before any stream capture begins.  Asynchronous.
+ */
+wdf_status wdf_global_attribution_noalloc(int32_t device, const float *phi, int64_t n, int64_t ldphi,
+                                          int32_t n_features, double *mean_abs, double *mean, void *stream);
+
+/*
  * Inspection, used by the tests.
  * wdf_debug_leaf_hist: the background pattern counts vc[l][p_b] (Eq.
  * "bg_shap_derivation" step (d)) of every leaf of the complete depth-D layout, as

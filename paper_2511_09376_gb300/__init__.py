@@ -20,6 +20,7 @@ from ._binding import (  # noqa: F401
     expected_value,
     explain,
     global_attribution,
+    global_attribution_noalloc,
     launch_count,
     library_path,
     load_ensemble,

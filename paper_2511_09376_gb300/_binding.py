@@ -36,6 +36,7 @@ for _name, _args in {
     "wdf_explain": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int, _vp, _c.c_int64, _vp],
     "wdf_expected_value": [_vp, _c.POINTER(_c.c_double), _vp],
     "wdf_global_attribution": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int32, _vp, _vp, _vp],
+    "wdf_global_attribution_noalloc": [_c.c_int32, _vp, _c.c_int64, _c.c_int64, _c.c_int32, _vp, _vp, _vp],
     "wdf_debug_leaf_hist": [_vp, _vp, _c.c_int64],
     "wdf_debug_shapley_table": [_vp, _c.c_int32, _vp, _vp],
 }.items():
@@ -218,6 +219,21 @@ def global_attribution(ctx: Context, phi, stream=None):
     mn = torch.empty(F, dtype=torch.float64, device=phi.device)
     _check(_lib.wdf_global_attribution(ctx.handle, _vp(phi.data_ptr()), int(n), int(phi.stride(0)), int(F),
                                        _vp(ma.data_ptr()), _vp(mn.data_ptr()), _stream_handle(stream)))
+    return ma, mn
+
+
+def global_attribution_noalloc(phi, stream=None):
+    """global_attribution without device allocation (fixed 2 MiB scratch inside the
+    library; see include/woodelf.h for its size limit and ordering rule)."""
+    torch = _torch()
+    if not (isinstance(phi, torch.Tensor) and phi.is_cuda and phi.dtype == torch.float32 and phi.stride(1) == 1):
+        raise ValueError("phi must be a float32 CUDA tensor with unit column stride")
+    n, F = phi.shape
+    ma = torch.empty(F, dtype=torch.float64, device=phi.device)
+    mn = torch.empty(F, dtype=torch.float64, device=phi.device)
+    _check(_lib.wdf_global_attribution_noalloc(int(phi.device.index or 0), _vp(phi.data_ptr()), int(n),
+                                               int(phi.stride(0)), int(F), _vp(ma.data_ptr()), _vp(mn.data_ptr()),
+                                               _stream_handle(stream)))
     return ma, mn
 
 

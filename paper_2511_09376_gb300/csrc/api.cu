@@ -72,6 +72,7 @@ std::atomic<int64_t> g_launches{0};
 
 namespace wdf {
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void set_last_error(const std::string &msg) { g_err = msg; }
 }  // namespace wdf
 
 struct wdf_ctx {

@@ -50,6 +50,9 @@ struct Packed {
 int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const float *thr, const int32_t *left,
                   const int32_t *right, const float *val, Packed *out, std::string *err);
 
+// Sets the thread-local message returned by wdf_last_error.
+void set_last_error(const std::string &msg);
+
 inline int slot_pad(int D) { return (D + 1) <= 4 ? 4 : ((D + 1) <= 8 ? 8 : 12); }
 
 }  // namespace wdf
