@@ -95,7 +95,10 @@ wdf_status wdf_ensemble_info(const wdf_ensemble *ens, wdf_info *out);
  * half of Algorithm 3: background pattern counts (step 1), pattern-pair tables (step
  * 2) and their contraction (step 3), in the given precision.  B is not retained.
  * WDF_EUNSUPPORTED: m == 0 (an empty background is the path-dependent variant).
- * Stream-ordered; a later wdf_explain on the same stream sees the result.
+ * precision WDF_TF32X3 / WDF_BF16X3 runs the contraction on the tensor cores (tcgen05,
+ * TMEM accumulators) and then waits for the stream to check the kernel's bounded waits:
+ * WDF_ETIMEOUT if one expired.  WDF_FP32 is stream-ordered without waiting; a later
+ * wdf_explain on the same stream sees the result.
  */
 wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, wdf_memkind kind,
                               wdf_precision precision, void *stream);

@@ -99,6 +99,11 @@ struct wdf_ensemble {
     int32_t *d_rn_count = nullptr;
     uint64_t *d_pt_mask = nullptr;
     float *d_zero = nullptr;  // 64 zero bytes: the entry a dead bottom subtree reads
+    // tensor-core contraction: K-major tables, 128-row tiles, wait-expiry flag
+    float *d_t32t = nullptr;
+    int4 *d_tiles128 = nullptr;
+    int n_tiles128 = 0;
+    int *d_err = nullptr;
     wdf::TreeArrays arrays() const {
         return wdf::TreeArrays{d_nodes, d_rn_key, d_rn_thr, d_rn_count, d_pt_mask, d_live};
     }
@@ -125,6 +130,7 @@ void free_ensemble(wdf_ensemble *e) {
     dfree(e->d_nodes); dfree(e->d_live); dfree(e->d_keys); dfree(e->d_group_leaf); dfree(e->d_leaf_row);
     dfree(e->d_w_rows); dfree(e->d_tiles); dfree(e->d_t32);
     dfree(e->d_rn_key); dfree(e->d_rn_thr); dfree(e->d_rn_count); dfree(e->d_pt_mask); dfree(e->d_zero);
+    dfree(e->d_t32t); dfree(e->d_tiles128); dfree(e->d_err);
     dfree(e->d_hist); dfree(e->d_vc); dfree(e->d_scale); dfree(e->d_S); dfree(e->d_sfold); dfree(e->d_base);
     for (int i = 0; i < 2; ++i) {
         dfree(e->d_stage_in[i]);
@@ -165,6 +171,33 @@ wdf_status ensure_staging(wdf_ensemble *e, int64_t rows, bool out) {
         e->stage_rows = rows;
     }
     (void)out;
+    return WDF_OK;
+}
+
+// K-major tables, 128-row tiles and the error flag for the tensor-core contraction.
+wdf_status ensure_tensor_core_state(wdf_ensemble *e) {
+    if (e->d_t32t) return WDF_OK;
+    const wdf::Packed &p = e->pk;
+    const int K = 1 << p.D, N = p.D << p.D;
+    std::vector<int4> tiles;
+    for (int gi = 0; gi < e->G; ++gi)
+        for (int r0 = p.group_off[(size_t)gi]; r0 < p.group_off[(size_t)gi + 1]; r0 += 128)
+            tiles.push_back(make_int4(gi, r0, std::min(r0 + 128, p.group_off[(size_t)gi + 1]), 0));
+    float *t32t = nullptr;
+    WDF_CUDA(dalloc(&t32t, (size_t)e->G * K * N, &e->bytes));
+    WDF_CUDA(dalloc(&e->d_tiles128, tiles.size(), &e->bytes));
+    WDF_CUDA(dalloc(&e->d_err, 1, &e->bytes));
+    WDF_CUDA(cudaMemset(e->d_err, 0, sizeof(int)));
+    if (!tiles.empty())
+        WDF_CUDA(cudaMemcpy(e->d_tiles128, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    float *scratch = nullptr;
+    WDF_CUDA(dalloc(&scratch, (size_t)e->G * K * N, &e->bytes));
+    WDF_CUDA(wdf::launch_tables(p.D, e->d_keys, e->G, scratch, nullptr, t32t, 0));
+    WDF_CUDA(cudaStreamSynchronize(0));
+    cudaFree(scratch);
+    e->bytes -= (int64_t)((size_t)e->G * K * N * sizeof(float));
+    e->d_t32t = t32t;
+    e->n_tiles128 = (int)tiles.size();
     return WDF_OK;
 }
 
@@ -273,7 +306,7 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
         chk(cudaMemset(e->d_zero, 0, 16 * sizeof(float)));
         if (e->n_tiles) chk(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
         // step 2 of Algorithm 3 depends only on the path signatures: build the tables now
-        chk(wdf::launch_tables(p.D, e->d_keys, e->G, e->d_t32, nullptr, 0));
+        chk(wdf::launch_tables(p.D, e->d_keys, e->G, e->d_t32, nullptr, nullptr, 0));
         chk(cudaStreamSynchronize(0));
     }
     if (ce != cudaSuccess) {
@@ -313,7 +346,8 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
     if (ldb < ens->pk.F) return fail(WDF_EINVAL, "ldb < n_features");
     if (m > (int64_t)0xFFFFFFFF) return fail(WDF_EUNSUPPORTED, "more than 2^32-1 background rows");
     if (kind != WDF_MEM_HOST && kind != WDF_MEM_DEVICE) return fail(WDF_EINVAL, "bad memory kind");
-    if (precision != WDF_FP32) return fail(WDF_EUNSUPPORTED, "only WDF_FP32 contraction is available");
+    if (precision != WDF_FP32 && precision != WDF_TF32X3 && precision != WDF_BF16X3)
+        return fail(WDF_EINVAL, "unknown precision");
     DeviceGuard g(ens->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const wdf::Packed &p = ens->pk;
@@ -328,6 +362,10 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
         WDF_CUDA(dalloc(&ens->d_base, 1, &ens->bytes));
     }
     ens->has_bg = 0;
+    if (precision != WDF_FP32) {
+        wdf_status s = ensure_tensor_core_state(ens);
+        if (s != WDF_OK) return s;
+    }
     WDF_CUDA(cudaMemsetAsync(ens->d_hist, 0, hist_n * 4, st));
     if (kind == WDF_MEM_DEVICE) {
         WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, p.F, ens->arrays(), p.T, ens->d_hist, ens->ctx->dev, st));
@@ -353,8 +391,18 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
     WDF_CUDA(wdf::launch_leaf_counts(p.D, ens->d_hist, ens->d_group_leaf, ens->n_live, ens->d_vc, st));
     WDF_CUDA(wdf::launch_scale(ens->d_w_rows, ens->n_live, m, ens->d_scale, st));
     WDF_CUDA(wdf::launch_base_value(p.D, ens->d_vc, ens->d_w_rows, ens->n_live, m, ens->d_base, st));
-    WDF_CUDA(wdf::launch_contract_fp32(p.D, ens->d_vc, ens->d_scale, ens->d_tiles, ens->n_tiles, ens->d_t32,
-                                       ens->d_S, st));
+    if (precision == WDF_FP32) {
+        WDF_CUDA(wdf::launch_contract_fp32(p.D, ens->d_vc, ens->d_scale, ens->d_tiles, ens->n_tiles, ens->d_t32,
+                                           ens->d_S, st));
+    } else {
+        WDF_CUDA(wdf::launch_contract_tc(p.D, precision == WDF_BF16X3 ? 1 : 0, ens->d_vc, ens->d_scale,
+                                         ens->d_tiles128, ens->n_tiles128, ens->d_t32t, ens->d_S, ens->d_err, st));
+        // a bounded wait inside the kernel that expired is reported here
+        int flag = 0;
+        WDF_CUDA(cudaMemcpyAsync(&flag, ens->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        WDF_CUDA(cudaStreamSynchronize(st));
+        if (flag) return fail(WDF_ETIMEOUT, "tensor-core contraction: an mbarrier wait expired");
+    }
     WDF_CUDA(wdf::launch_fold(p.D, ens->d_S, ens->d_leaf_row, p.T, ens->d_sfold, st));
     if (kind == WDF_MEM_HOST) WDF_CUDA(cudaStreamSynchronize(st));
     ens->m = m;
@@ -470,7 +518,7 @@ wdf_status wdf_debug_shapley_table(wdf_ctx *ctx, int32_t depth, const int32_t *f
     if (ce == cudaSuccess) ce = dalloc(&d_t32, K * N, &dummy);
     if (ce == cudaSuccess) ce = dalloc(&d_t64, K * N, &dummy);
     if (ce == cudaSuccess) ce = cudaMemcpy(d_key, &key, 4, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = wdf::launch_tables(depth, d_key, 1, d_t32, d_t64, 0);
+    if (ce == cudaSuccess) ce = wdf::launch_tables(depth, d_key, 1, d_t32, d_t64, nullptr, 0);
     if (ce == cudaSuccess) ce = cudaMemcpy(out, d_t64, K * N * sizeof(double), cudaMemcpyDeviceToHost);
     dfree(d_key);
     dfree(d_t32);

@@ -20,7 +20,8 @@ __device__ __forceinline__ double binom_small(int n, int k) {
 // path position k); its unit-weight Shapley value is Formula "shap_simplified_formula"
 // in FP64 from exact binomials.  A feature met at several path positions is one
 // variable (cubes are sets); its value sits at its first position.
-__global__ void k_tables(int D, const uint32_t *__restrict__ keys, float *__restrict__ t32, double *__restrict__ t64) {
+__global__ void k_tables(int D, const uint32_t *__restrict__ keys, float *__restrict__ t32, double *__restrict__ t64,
+                         float *__restrict__ t32t) {
     const int g = blockIdx.y;
     const int K = 1 << D, N = D << D;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -49,14 +50,17 @@ __global__ void k_tables(int D, const uint32_t *__restrict__ keys, float *__rest
         }
         t32[rowbase + ((size_t)k << D) + pc] = (float)v;
         if (t64) t64[rowbase + ((size_t)k << D) + pc] = v;
+        // K-major copy [g][column][p_b] for the tensor-core contraction
+        if (t32t) t32t[((size_t)g * N + ((size_t)k << D) + pc) * K + pb] = (float)v;
     }
 }
 
-cudaError_t launch_tables(int D, const uint32_t *sig_keys, int G, float *t32, double *t64, cudaStream_t st) {
+cudaError_t launch_tables(int D, const uint32_t *sig_keys, int G, float *t32, double *t64, float *t32t,
+                          cudaStream_t st) {
     if (G == 0) return cudaSuccess;
     const int total = 1 << (2 * D);
     dim3 grid((total + 255) / 256, G);
-    k_tables<<<grid, 256, 0, st>>>(D, sig_keys, t32, t64);
+    k_tables<<<grid, 256, 0, st>>>(D, sig_keys, t32, t64, t32t);
     count_launches(1);
     return cudaGetLastError();
 }

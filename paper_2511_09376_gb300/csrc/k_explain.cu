@@ -24,7 +24,11 @@ namespace wdf {
 template <int D>
 struct ExplainCfg {
     static constexpr int TCH = 8;  // trees per shared-memory chunk
-    static constexpr int GS = (Shape<D>::NS * Shape<D>::SP <= 128) ? Shape<D>::NS : (64 / Shape<D>::SP);
+    // bottom subtrees gathered together: the largest power of two (a divisor of NS) whose
+    // slot vectors fit in 128 registers
+    static constexpr int gs(int g) { return (g > 1 && g * Shape<D>::SP > 128) ? gs(g / 2) : g; }
+    static constexpr int GS = gs(Shape<D>::NS);
+    static_assert(Shape<D>::NS % GS == 0, "gather groups must tile the bottom subtrees");
 };
 
 template <int D>

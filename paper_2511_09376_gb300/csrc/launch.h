@@ -35,8 +35,9 @@ cudaError_t launch_leaf_counts(int D, const uint32_t *hist, const int32_t *group
                                cudaStream_t st);
 
 // Step 2: FP64 pattern-pair tables of G path signatures; t32 (and t64 when non-null)
-// laid out [G][2^D][D * 2^D].
-cudaError_t launch_tables(int D, const uint32_t *sig_keys, int G, float *t32, double *t64, cudaStream_t st);
+// laid out [G][2^D][D * 2^D]; t32t (when non-null) the K-major copy [G][D * 2^D][2^D].
+cudaError_t launch_tables(int D, const uint32_t *sig_keys, int G, float *t32, double *t64, float *t32t,
+                          cudaStream_t st);
 
 // Split copies of the FP32 tables for the tensor-core contraction: hi + lo with hi
 // rounded to TF32 (bf16 == 0) or BF16 (bf16 == 1); n elements.
@@ -47,6 +48,13 @@ cudaError_t launch_split(const float *src, int64_t n, int bf16, void *hi, void *
 // row_end, 0) work items of up to 64 rows.
 cudaError_t launch_contract_fp32(int D, const uint32_t *vc, const float *scale, const int4 *tiles, int n_tiles,
                                  const float *t32, float *S, cudaStream_t st);
+
+// Step 3 on the tensor cores (tcgen05, TMEM accumulators): the same S as
+// launch_contract_fp32 from split-precision operands, TF32 (bf16 == 0) or BF16 (1).
+// tiles: (group, row0, row_end, 0) work items of up to 128 rows; t32t the K-major tables.
+// err is set to 1 if a bounded wait expired.
+cudaError_t launch_contract_tc(int D, int bf16, const uint32_t *vc, const float *scale, const int4 *tiles, int n_tiles,
+                               const float *t32t, float *S, int *err, cudaStream_t st);
 
 // Folds the per-leaf S rows of every bottom subtree into per-entry slot vectors
 // sfold[T][NS][2^(D+1)][SP] (see wdf_internal.h).
