@@ -128,6 +128,38 @@ wdf_status wdf_global_attribution(wdf_ctx *ctx, const float *phi, int64_t n, int
                                   double *mean_abs, double *mean, void *stream);
 
 /*
+ * Ragged batches (project addition; the paper runs one tree ensemble at a time).
+ * A batch groups ensembles of one context -- any depths 2..8 and feature counts -- so a
+ * single call explains many requests against them with ONE CUDA-graph launch: the graph
+ * copies a packed work description (one memcpy) and runs a persistent consumer kernel
+ * per depth class on parallel branches over (ensemble, request, tile of consumer rows)
+ * work items.  Per-row results equal those of wdf_explain bit for bit.
+ *
+ * wdf_batch_create: the ensembles must outlive the batch; their backgrounds may be set
+ * (or reset) later but before wdf_batch_explain.
+ * wdf_batch_explain: request i explains n[i] rows at C[i] (device memory, row stride
+ * ldc[i]) against ensembles[ensemble_index[i]] into phi[i] (device, stride ldphi[i]).
+ * Stream-ordered and asynchronous; the caller may reuse its request arrays on return.
+ * WDF_EINVAL for an index out of range, a missing background or bad sizes.
+ * wdf_batch_autotune: runs each depth class's kernel on the given requests with every
+ * consumer-tile size that fits (32, 64, 128 rows), reps timed runs each, and keeps the
+ * fastest per class (phi is written with valid results).  cache_path (nullable): a text
+ * file of "depth features_rounded_up_to_32 tile_rows ms" lines read first and appended
+ * to.  Synchronous.  wdf_batch_tile_rows reports the tile size of a depth class (-1 if
+ * the batch has none).
+ */
+typedef struct wdf_batch wdf_batch;
+wdf_status wdf_batch_create(wdf_ctx *ctx, int32_t n_ensembles, wdf_ensemble *const *ensembles, wdf_batch **out);
+void wdf_batch_destroy(wdf_batch *batch);
+wdf_status wdf_batch_explain(wdf_batch *batch, int32_t n_requests, const int32_t *ensemble_index,
+                             const float *const *C, const int64_t *n, const int64_t *ldc, float *const *phi,
+                             const int64_t *ldphi, void *stream);
+wdf_status wdf_batch_autotune(wdf_batch *batch, int32_t n_requests, const int32_t *ensemble_index,
+                              const float *const *C, const int64_t *n, const int64_t *ldc, float *const *phi,
+                              const int64_t *ldphi, int32_t reps, const char *cache_path, void *stream);
+wdf_status wdf_batch_tile_rows(const wdf_batch *batch, int32_t depth, int32_t *tile_rows);
+
+/*
  * wdf_global_attribution without any device allocation.  The paper has no counterpart:
  * this is a service for callers that cannot allocate device memory when they need the
  * reduction -- code running under a framework whose caching allocator already holds the

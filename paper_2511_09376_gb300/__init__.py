@@ -8,6 +8,11 @@ library.  If the library has not been built, importing the binding raises.
 """
 from ._binding import (  # noqa: F401
     BF16X3,
+    Batch,
+    batch_autotune,
+    batch_create,
+    batch_explain,
+    batch_tile_rows,
     FP32,
     TF32X3,
     Context,

@@ -38,6 +38,10 @@ for _name, _args in {
     "wdf_global_attribution": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int32, _vp, _vp, _vp],
     "wdf_global_attribution_noalloc": [_c.c_int32, _vp, _c.c_int64, _c.c_int64, _c.c_int32, _vp, _vp, _vp],
     "wdf_debug_leaf_hist": [_vp, _vp, _c.c_int64],
+    "wdf_batch_create": [_vp, _c.c_int32, _vp, _c.POINTER(_vp)],
+    "wdf_batch_explain": [_vp, _c.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "wdf_batch_autotune": [_vp, _c.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _c.c_int32, _c.c_char_p, _vp],
+    "wdf_batch_tile_rows": [_vp, _c.c_int32, _c.POINTER(_c.c_int32)],
     "wdf_debug_shapley_table": [_vp, _c.c_int32, _vp, _vp],
 }.items():
     getattr(_lib, _name).argtypes = _args
@@ -48,6 +52,8 @@ _lib.wdf_ctx_destroy.argtypes = [_vp]
 _lib.wdf_ctx_destroy.restype = None
 _lib.wdf_ensemble_destroy.argtypes = [_vp]
 _lib.wdf_ensemble_destroy.restype = None
+_lib.wdf_batch_destroy.argtypes = [_vp]
+_lib.wdf_batch_destroy.restype = None
 
 
 class WdfError(RuntimeError):
@@ -165,10 +171,10 @@ def _matrix(x):
     """(pointer, rows, leading dim, memkind, keepalive) of a row-major float32 matrix."""
     torch = _torch()
     if isinstance(x, torch.Tensor):
-        if x.dtype != torch.float32 or x.dim() != 2 or x.stride(1) != 1:
+        if x.dtype != torch.float32 or x.dim() != 2 or (x.numel() > 0 and x.stride(1) != 1):
             raise ValueError("expected a 2-D float32 tensor with unit column stride")
         kind = MEM_DEVICE if x.is_cuda else MEM_HOST
-        return x.data_ptr(), x.shape[0], x.stride(0), kind, x
+        return x.data_ptr(), x.shape[0], max(x.stride(0), x.shape[1]), kind, x
     a = np.asarray(x)
     if a.dtype != np.float32 or a.ndim != 2 or a.strides[1] != 4 or a.strides[0] % 4:
         a = np.ascontiguousarray(a, dtype=np.float32)
@@ -251,3 +257,74 @@ def debug_shapley_table(ctx: Context, first) -> np.ndarray:
     out = np.zeros((1 << D, D << D), dtype=np.float64)
     _check(_lib.wdf_debug_shapley_table(ctx.handle, D, _vp(f.ctypes.data), _vp(out.ctypes.data)))
     return out
+
+
+class Batch:
+    def __init__(self, ctx: Context, ensembles, handle):
+        self.ctx = ctx
+        self.ensembles = list(ensembles)  # kept alive with the batch
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            _lib.wdf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_create(ctx: Context, ensembles) -> Batch:
+    hs = (_vp * len(ensembles))(*[e.handle for e in ensembles])
+    h = _vp()
+    _check(_lib.wdf_batch_create(ctx.handle, len(ensembles), hs, _c.byref(h)))
+    return Batch(ctx, ensembles, h)
+
+
+def _batch_args(batch, requests, outs):
+    """requests: list of (ensemble index, C device tensor); outs: phi tensors or None."""
+    torch = _torch()
+    k = len(requests)
+    if outs is None:
+        outs = []
+        for i, C in requests:
+            F = ensemble_info(batch.ensembles[i])["n_features"]
+            outs.append(torch.empty((C.shape[0], F), dtype=torch.float32, device=C.device))
+    for (i, C), o in zip(requests, outs):
+        if not (C.is_cuda and o.is_cuda and C.dtype == torch.float32 and o.dtype == torch.float32
+                and (C.numel() == 0 or C.stride(1) == 1) and (o.numel() == 0 or o.stride(1) == 1)):
+            raise ValueError("batch requests take float32 CUDA tensors with unit column stride")
+    idx = np.array([i for i, _ in requests], dtype=np.int32)
+    cp = np.array([C.data_ptr() for _, C in requests], dtype=np.uint64)
+    pp = np.array([o.data_ptr() for o in outs], dtype=np.uint64)
+    n = np.array([C.shape[0] for _, C in requests], dtype=np.int64)
+    ldc = np.array([max(C.stride(0), C.shape[1]) for _, C in requests], dtype=np.int64)
+    ldp = np.array([max(o.stride(0), o.shape[1]) for o in outs], dtype=np.int64)
+    arrs = (idx, cp, n, ldc, pp, ldp)
+    return k, arrs, outs
+
+
+def batch_explain(batch: Batch, requests, outs=None, stream=None):
+    """One graph launch for all requests; returns the phi tensors (asynchronous)."""
+    k, (idx, cp, n, ldc, pp, ldp), outs = _batch_args(batch, requests, outs)
+    _check(_lib.wdf_batch_explain(batch.handle, k, _vp(idx.ctypes.data), _vp(cp.ctypes.data), _vp(n.ctypes.data),
+                                  _vp(ldc.ctypes.data), _vp(pp.ctypes.data), _vp(ldp.ctypes.data),
+                                  _stream_handle(stream)))
+    return outs
+
+
+def batch_autotune(batch: Batch, requests, outs=None, reps=3, cache_path=None, stream=None):
+    k, (idx, cp, n, ldc, pp, ldp), outs = _batch_args(batch, requests, outs)
+    _check(_lib.wdf_batch_autotune(batch.handle, k, _vp(idx.ctypes.data), _vp(cp.ctypes.data), _vp(n.ctypes.data),
+                                   _vp(ldc.ctypes.data), _vp(pp.ctypes.data), _vp(ldp.ctypes.data), int(reps),
+                                   cache_path.encode() if cache_path else None, _stream_handle(stream)))
+    return outs
+
+
+def batch_tile_rows(batch: Batch, depth: int) -> int:
+    v = _c.c_int32(0)
+    _check(_lib.wdf_batch_tile_rows(batch.handle, int(depth), _c.byref(v)))
+    return int(v.value)

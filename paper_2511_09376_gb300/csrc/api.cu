@@ -75,54 +75,7 @@ void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed);
 void set_last_error(const std::string &msg) { g_err = msg; }
 }  // namespace wdf
 
-struct wdf_ctx {
-    int device = 0;
-    wdf::DevInfo dev;
-};
-
-struct wdf_ensemble {
-    wdf_ctx *ctx = nullptr;
-    wdf::Packed pk;
-    int G = 0, n_live = 0, n_tiles = 0;
-    int64_t bytes = 0;
-    // ensemble (load time)
-    int2 *d_nodes = nullptr;
-    uint64_t *d_live = nullptr;
-    uint32_t *d_keys = nullptr;
-    int32_t *d_group_leaf = nullptr;
-    int32_t *d_leaf_row = nullptr;
-    double *d_w_rows = nullptr;
-    int4 *d_tiles = nullptr;
-    float *d_t32 = nullptr;
-    int32_t *d_rn_key = nullptr;
-    float *d_rn_thr = nullptr;
-    int32_t *d_rn_count = nullptr;
-    uint64_t *d_pt_mask = nullptr;
-    float *d_zero = nullptr;  // 64 zero bytes: the entry a dead bottom subtree reads
-    // tensor-core contraction: K-major tables, 128-row tiles, wait-expiry flag
-    float *d_t32t = nullptr;
-    int4 *d_tiles128 = nullptr;
-    int n_tiles128 = 0;
-    int *d_err = nullptr;
-    wdf::TreeArrays arrays() const {
-        return wdf::TreeArrays{d_nodes, d_rn_key, d_rn_thr, d_rn_count, d_pt_mask, d_live};
-    }
-    // background state (set_background)
-    int has_bg = 0;
-    int64_t m = 0;
-    uint32_t *d_hist = nullptr;
-    uint32_t *d_vc = nullptr;
-    float *d_scale = nullptr;
-    float *d_S = nullptr;
-    float *d_sfold = nullptr;
-    double *d_base = nullptr;
-    // staging for host-memory calls: two buffers per direction, one per internal stream
-    float *d_stage_in[2] = {nullptr, nullptr};
-    float *d_stage_out[2] = {nullptr, nullptr};
-    int64_t stage_rows = 0;
-    cudaStream_t ist[2] = {nullptr, nullptr};
-    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
-};
+#include "wdf_objects.h"
 
 namespace {
 
@@ -423,8 +376,7 @@ wdf_status wdf_explain(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc
     DeviceGuard g(ens->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (kind == WDF_MEM_DEVICE) {
-        WDF_CUDA(wdf::launch_explain(p.D, C, n, ldc, p.F, ens->arrays(), ens->d_sfold, ens->d_zero, p.T, phi, ldphi,
-                                     ens->ctx->dev, st));
+        WDF_CUDA(wdf::launch_explain(p.D, C, n, ldc, ens->job(), phi, ldphi, 0, ens->ctx->dev, st));
         return WDF_OK;
     }
     wdf_status s = ensure_staging(ens, n, true);
@@ -437,8 +389,8 @@ wdf_status wdf_explain(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc
         const int b = (int)(chunk & 1);
         cudaStream_t sb = ens->ist[b];
         WDF_CUDA(copy_rows(ens->d_stage_in[b], p.F, C + r0 * ldc, ldc, rows, p.F, cudaMemcpyHostToDevice, sb));
-        WDF_CUDA(wdf::launch_explain(p.D, ens->d_stage_in[b], rows, p.F, p.F, ens->arrays(), ens->d_sfold,
-                                     ens->d_zero, p.T, ens->d_stage_out[b], p.F, ens->ctx->dev, sb));
+        WDF_CUDA(wdf::launch_explain(p.D, ens->d_stage_in[b], rows, p.F, ens->job(), ens->d_stage_out[b], p.F, 0,
+                                     ens->ctx->dev, sb));
         WDF_CUDA(copy_rows(phi + r0 * ldphi, ldphi, ens->d_stage_out[b], p.F, rows, p.F, cudaMemcpyDeviceToHost, sb));
     }
     for (int i = 0; i < 2; ++i) {

@@ -60,18 +60,20 @@ __device__ __forceinline__ void ldg_f8(const float4 *p, float4 &a, float4 &b) {
                  : "l"(p));
 }
 
+// One tile of TC consumer rows starting at row c0 of C (n rows), for one ensemble.
 template <int D, int TC>
-__global__ void __launch_bounds__(TC) k_explain(const float *__restrict__ C, int64_t n, int64_t ldc, int F,
-                                                TreeArrays ta, const float *__restrict__ sfold,
-                                                const float *__restrict__ zero, int T, float *__restrict__ phi,
-                                                int64_t ldp) {
+__device__ __forceinline__ void explain_tile(const ExplainJob &job, const float *__restrict__ C, int64_t n,
+                                             int64_t ldc, float *__restrict__ phi, int64_t ldp, int64_t c0,
+                                             unsigned char *smem_raw) {
     using S = Shape<D>;
     using X = ExplainCfg<D>;
     constexpr int XS = TC + 1;
     constexpr int NA = S::NS > 1 ? S::NS - 1 : 1;
     constexpr int GS = X::GS;
     constexpr int Q = S::SP / 4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int F = job.F, T = job.T;
+    const TreeArrays &ta = job.ta;
+    const float *__restrict__ sfold = job.sfold;
     const ExLayout<D> L(F, TC);
     float *sx = reinterpret_cast<float *>(smem_raw);
     float *sp = reinterpret_cast<float *>(smem_raw + L.x);
@@ -80,7 +82,6 @@ __global__ void __launch_bounds__(TC) k_explain(const float *__restrict__ C, int
     int *sfo = reinterpret_cast<int *>(smem_raw + 2 * L.x + L.meta + L.rn);
     int *sf3 = reinterpret_cast<int *>(smem_raw + 2 * L.x + L.meta + L.rn + L.fo);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t c0 = (int64_t)blockIdx.x * TC;
     for (int r = warp; r < TC; r += TC / 32) {
         const int64_t row = c0 + r;
         const float *src = C + row * ldc;
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(TC) k_explain(const float *__restrict__ C, int
     for (int i = tid; i < (F + 1) * XS; i += TC) sp[i] = 0.0f;
     sx[F * XS + tid] = 0.0f;
     float *myphi = sp + tid;
-    const float4 *z4 = reinterpret_cast<const float4 *>(zero);
+    const float4 *z4 = reinterpret_cast<const float4 *>(job.zero);
     for (int tc0 = 0; tc0 < T; tc0 += X::TCH) {
         const int tcn = min(X::TCH, T - tc0);
         __syncthreads();
@@ -161,41 +162,144 @@ __global__ void __launch_bounds__(TC) k_explain(const float *__restrict__ C, int
     }
 }
 
+
 template <int D, int TC>
-static cudaError_t explain_t(const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, const float *sfold,
-                             const float *zero, int T, float *phi, int64_t ldp, const DevInfo &dev, cudaStream_t st) {
-    const size_t smem = ExLayout<D>(F, TC).total;
+__global__ void __launch_bounds__(TC) k_explain(const float *__restrict__ C, int64_t n, int64_t ldc, ExplainJob job,
+                                                float *__restrict__ phi, int64_t ldp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    explain_tile<D, TC>(job, C, n, ldc, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
+}
+
+// Persistent form over a ragged batch: work item i is (job, request, first row) and
+// block b takes items b, b + gridDim.x, ...  The item count is read from device memory
+// so one captured graph serves batches of any size up to its capacity.
+template <int D, int TC>
+__global__ void __launch_bounds__(TC) k_explain_batch(const ExplainJob *__restrict__ jobs,
+                                                      const BatchRequest *__restrict__ reqs,
+                                                      const int4 *__restrict__ items, const int *__restrict__ n_items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int count = *n_items;
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const int4 it = items[i];
+        const ExplainJob job = jobs[it.x];
+        const BatchRequest rq = reqs[it.y];
+        const int64_t c0 = ((int64_t)it.z << 31) | (uint32_t)it.w;
+        explain_tile<D, TC>(job, rq.C, rq.n, rq.ldc, rq.phi, rq.ldp, c0, smem_raw);
+        __syncthreads();
+    }
+}
+
+template <int D, int TC>
+static cudaError_t explain_t(const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi, int64_t ldp,
+                             const DevInfo &dev, cudaStream_t st) {
+    const size_t smem = ExLayout<D>(job.F, TC).total;
     if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
     auto kern = k_explain<D, TC>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     const int64_t blocks = (n + TC - 1) / TC;
-    kern<<<(unsigned)blocks, TC, smem, st>>>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp);
+    kern<<<(unsigned)blocks, TC, smem, st>>>(C, n, ldc, job, phi, ldp);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int default_tile_rows(int D, int F, const DevInfo &dev) {
+    size_t s64 = 0;
+    switch (D) {
+        case 2: s64 = ExLayout<2>(F, 64).total; break;
+        case 3: s64 = ExLayout<3>(F, 64).total; break;
+        case 4: s64 = ExLayout<4>(F, 64).total; break;
+        case 5: s64 = ExLayout<5>(F, 64).total; break;
+        case 6: s64 = ExLayout<6>(F, 64).total; break;
+        case 7: s64 = ExLayout<7>(F, 64).total; break;
+        default: s64 = ExLayout<8>(F, 64).total; break;
+    }
+    return s64 <= dev.smem_optin / 2 ? 64 : 32;
+}
+
+template <int D>
+static cudaError_t explain_d(const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi, int64_t ldp,
+                             int tile_rows, const DevInfo &dev, cudaStream_t st) {
+    switch (tile_rows) {
+        case 32: return explain_t<D, 32>(C, n, ldc, job, phi, ldp, dev, st);
+        case 128: return explain_t<D, 128>(C, n, ldc, job, phi, ldp, dev, st);
+        default: return explain_t<D, 64>(C, n, ldc, job, phi, ldp, dev, st);
+    }
+}
+
+cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi,
+                           int64_t ldp, int tile_rows, const DevInfo &dev, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (tile_rows <= 0) tile_rows = default_tile_rows(D, job.F, dev);
+    switch (D) {
+        case 2: return explain_d<2>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
+        case 3: return explain_d<3>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
+        case 4: return explain_d<4>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
+        case 5: return explain_d<5>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
+        case 6: return explain_d<6>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
+        case 7: return explain_d<7>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
+        case 8: return explain_d<8>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int D, int TC>
+static cudaError_t batch_t(const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items, const int *n_items,
+                           int F_max, int grid, const DevInfo &dev, cudaStream_t st) {
+    const size_t smem = ExLayout<D>(F_max, TC).total;
+    if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
+    auto kern = k_explain_batch<D, TC>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    if (grid <= 0) {
+        int per_sm = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC, smem);
+        if (err != cudaSuccess) return err;
+        grid = dev.sms * (per_sm > 0 ? per_sm : 1);
+    }
+    kern<<<grid, TC, smem, st>>>(jobs, reqs, items, n_items);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int D>
-static cudaError_t explain_d(const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, const float *sfold,
-                             const float *zero, int T, float *phi, int64_t ldp, const DevInfo &dev, cudaStream_t st) {
-    if (ExLayout<D>(F, 64).total <= dev.smem_optin / 2)
-        return explain_t<D, 64>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
-    return explain_t<D, 32>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
+static cudaError_t batch_d(const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items, const int *n_items,
+                           int F_max, int tile_rows, int grid, const DevInfo &dev, cudaStream_t st) {
+    switch (tile_rows) {
+        case 32: return batch_t<D, 32>(jobs, reqs, items, n_items, F_max, grid, dev, st);
+        case 128: return batch_t<D, 128>(jobs, reqs, items, n_items, F_max, grid, dev, st);
+        default: return batch_t<D, 64>(jobs, reqs, items, n_items, F_max, grid, dev, st);
+    }
 }
 
-cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta,
-                           const float *sfold, const float *zero, int T, float *phi, int64_t ldp,
-                           const DevInfo &dev, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
+cudaError_t launch_explain_batch(int D, const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items,
+                                 const int *n_items, int F_max, int tile_rows, int grid, const DevInfo &dev,
+                                 cudaStream_t st) {
     switch (D) {
-        case 2: return explain_d<2>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
-        case 3: return explain_d<3>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
-        case 4: return explain_d<4>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
-        case 5: return explain_d<5>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
-        case 6: return explain_d<6>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
-        case 7: return explain_d<7>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
-        case 8: return explain_d<8>(C, n, ldc, F, ta, sfold, zero, T, phi, ldp, dev, st);
+        case 2: return batch_d<2>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
+        case 3: return batch_d<3>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
+        case 4: return batch_d<4>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
+        case 5: return batch_d<5>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
+        case 6: return batch_d<6>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
+        case 7: return batch_d<7>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
+        case 8: return batch_d<8>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t explain_smem_bytes(int D, int F, int tile_rows) {
+    switch (D * 1000 + tile_rows) {
+#define WDF_SMEM_CASE(d, tc) \
+    case d * 1000 + tc: return ExLayout<d>(F, tc).total;
+        WDF_SMEM_CASE(2, 32) WDF_SMEM_CASE(2, 64) WDF_SMEM_CASE(2, 128)
+        WDF_SMEM_CASE(3, 32) WDF_SMEM_CASE(3, 64) WDF_SMEM_CASE(3, 128)
+        WDF_SMEM_CASE(4, 32) WDF_SMEM_CASE(4, 64) WDF_SMEM_CASE(4, 128)
+        WDF_SMEM_CASE(5, 32) WDF_SMEM_CASE(5, 64) WDF_SMEM_CASE(5, 128)
+        WDF_SMEM_CASE(6, 32) WDF_SMEM_CASE(6, 64) WDF_SMEM_CASE(6, 128)
+        WDF_SMEM_CASE(7, 32) WDF_SMEM_CASE(7, 64) WDF_SMEM_CASE(7, 128)
+        WDF_SMEM_CASE(8, 32) WDF_SMEM_CASE(8, 64) WDF_SMEM_CASE(8, 128)
+#undef WDF_SMEM_CASE
+        default: return (size_t)-1;
     }
 }
 

@@ -19,6 +19,21 @@ struct TreeArrays {
     const uint64_t *live;     // [T]
 };
 
+// Everything the consumer kernel needs about one ensemble.
+struct ExplainJob {
+    TreeArrays ta;
+    const float *sfold;  // folded slot vectors [T][NS][2^(D+1)][SP]
+    const float *zero;   // 64 zero bytes
+    int T, F;
+};
+
+// One request of a ragged batch: n consumer rows at C (row stride ldc), phi out.
+struct BatchRequest {
+    const float *C;
+    float *phi;
+    int64_t n, ldc, ldp;
+};
+
 struct DevInfo {
     int sms = 0;
     size_t smem_optin = 0;  // max dynamic shared memory per block
@@ -67,10 +82,19 @@ cudaError_t launch_scale(const double *w, int n_live, int64_t m, float *scale, c
 cudaError_t launch_base_value(int D, const uint32_t *vc, const double *leaf_w_rows, int n_live, int64_t m,
                               double *out, cudaStream_t st);
 
-// Step 4: phi of n consumer rows.  zero: 64 bytes of zeros (the entry of a dead subtree).
-cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta,
-                           const float *sfold, const float *zero, int T, float *phi, int64_t ldp,
-                           const DevInfo &dev, cudaStream_t st);
+// Step 4: phi of n consumer rows, tile_rows consumer rows per block (32, 64 or 128;
+// 0 picks the default for the shared-memory budget).
+cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi,
+                           int64_t ldp, int tile_rows, const DevInfo &dev, cudaStream_t st);
+int default_tile_rows(int D, int F, const DevInfo &dev);
+size_t explain_smem_bytes(int D, int F, int tile_rows);
+
+// Step 4 for a ragged batch of one depth: a persistent grid (grid <= 0: one wave at full
+// occupancy) walks the work items (job, request, first row split as hi/lo words);
+// *n_items is read on the device.  F_max bounds the feature count of every job.
+cudaError_t launch_explain_batch(int D, const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items,
+                                 const int *n_items, int F_max, int tile_rows, int grid, const DevInfo &dev,
+                                 cudaStream_t st);
 
 // FP64 column means of |phi| and phi: partial sums per row block, then a fixed-order
 // final sum.  partial holds n_blocks * F * 2 doubles.

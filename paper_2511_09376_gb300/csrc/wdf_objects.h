@@ -1,0 +1,57 @@
+// Library object definitions shared by the C-ABI translation units (internal).
+#pragma once
+#include <cstdint>
+
+#include "launch.h"
+#include "wdf_internal.h"
+
+struct wdf_ctx {
+    int device = 0;
+    wdf::DevInfo dev;
+};
+
+struct wdf_ensemble {
+    wdf_ctx *ctx = nullptr;
+    wdf::Packed pk;
+    int G = 0, n_live = 0, n_tiles = 0;
+    int64_t bytes = 0;
+    // ensemble (load time)
+    int2 *d_nodes = nullptr;
+    uint64_t *d_live = nullptr;
+    uint32_t *d_keys = nullptr;
+    int32_t *d_group_leaf = nullptr;
+    int32_t *d_leaf_row = nullptr;
+    double *d_w_rows = nullptr;
+    int4 *d_tiles = nullptr;
+    float *d_t32 = nullptr;
+    int32_t *d_rn_key = nullptr;
+    float *d_rn_thr = nullptr;
+    int32_t *d_rn_count = nullptr;
+    uint64_t *d_pt_mask = nullptr;
+    float *d_zero = nullptr;  // 64 zero bytes: the entry a dead bottom subtree reads
+    // tensor-core contraction: K-major tables, 128-row tiles, wait-expiry flag
+    float *d_t32t = nullptr;
+    int4 *d_tiles128 = nullptr;
+    int n_tiles128 = 0;
+    int *d_err = nullptr;
+    wdf::TreeArrays arrays() const {
+        return wdf::TreeArrays{d_nodes, d_rn_key, d_rn_thr, d_rn_count, d_pt_mask, d_live};
+    }
+    wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, d_zero, pk.T, pk.F}; }
+    // background state (set_background)
+    int has_bg = 0;
+    int64_t m = 0;
+    uint32_t *d_hist = nullptr;
+    uint32_t *d_vc = nullptr;
+    float *d_scale = nullptr;
+    float *d_S = nullptr;
+    float *d_sfold = nullptr;
+    double *d_base = nullptr;
+    // staging for host-memory calls: two buffers per direction, one per internal stream
+    float *d_stage_in[2] = {nullptr, nullptr};
+    float *d_stage_out[2] = {nullptr, nullptr};
+    int64_t stage_rows = 0;
+    cudaStream_t ist[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+};
+
