@@ -321,6 +321,152 @@ def run_reference(args, world, rank):
     }
 
 
+def run_ragged(args):
+    """64 ensembles of mixed depth/width: the plain path (one wdf_explain per ensemble, FP32
+    contraction) against the batched form (one autotuned graph launch over all of them,
+    BF16 split-precision contraction)."""
+    import torch
+
+    import paper_2511_09376_gb300 as wdf
+    from paper_2511_09376_gb300 import synth
+    specs = synth.ragged_specs()
+    ctx = wdf.ctx_create(0)
+    dev = torch.device("cuda", 0)
+    ens, Cs, t_bg = [], [], {"fp32": 0.0, "bf16x3": 0.0}
+    plain_e, batch_e = [], []
+    t0 = time.time()
+    for w in specs:
+        e_np, C, B = synth.make(w)
+        dB = torch.from_numpy(B).to(dev)
+        e_plain = wdf.load_ensemble(ctx, e_np)
+        e_batch = wdf.load_ensemble(ctx, e_np)
+        for e, prec in ((e_plain, "fp32"), (e_batch, "bf16x3")):
+            torch.cuda.synchronize()
+            s = time.perf_counter()
+            wdf.set_background(e, dB, prec)
+            torch.cuda.synchronize()
+            t_bg[prec] += time.perf_counter() - s
+        plain_e.append(e_plain)
+        batch_e.append(e_batch)
+        Cs.append(torch.from_numpy(C).to(dev))
+        del dB, B
+    gen_s = time.time() - t0
+    rows = sum(c.shape[0] for c in Cs)
+    outs_p = [torch.empty((c.shape[0], e.info["n_features"]), device=dev) for c, e in zip(Cs, plain_e)]
+    outs_b = [torch.empty_like(o) for o in outs_p]
+    batch = wdf.batch_create(ctx, batch_e)
+    reqs = list(enumerate(Cs))
+    wdf.batch_autotune(batch, reqs, outs=outs_b, reps=2)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def plain():
+        for e, c, o in zip(plain_e, Cs, outs_p):
+            wdf.explain(e, c, out=o)
+
+    def batched():
+        wdf.batch_explain(batch, reqs, outs=outs_b)
+
+    for _ in range(args.warmup):
+        plain()
+        batched()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        plain()
+    ev[1].record(stream)
+    for _ in range(args.steps):
+        batched()
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    batch_ms = ev[1].elapsed_time(ev[2]) / args.steps
+    diff = max(float((a - b).abs().max()) for a, b in zip(outs_p, outs_b))
+    tiles = {d: wdf.batch_tile_rows(batch, d) for d in range(2, 9)}
+    return {
+        "metric": METRIC, "value": rows / (batch_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"ragged batch: {len(specs)} ensembles, trees 10-500, depth 2-8, features 20-300, "
+                               f"{rows} consumer rows in total", "contraction": "bf16x3 (batched) vs fp32 (plain)"},
+        "plain_rows_per_s": rows / (plain_ms * 1e-3), "plain_ms": plain_ms, "batched_ms": batch_ms,
+        "speedup_batched_vs_plain": plain_ms / batch_ms, "max_abs_diff_batched_vs_plain": diff,
+        "background_s": t_bg, "tile_rows": tiles, "generate_s": gen_s,
+        "graph_launches_per_step_batched": 1,
+        "kernels_per_step_batched": len([d for d in tiles.values() if d > 0]),
+        "kernels_per_step_plain": len(specs),
+    }
+
+
+def run_serving(args):
+    """Poisson request stream (200 req/s, rows log-uniform 1..1e5) against four resident
+    ensembles (50/200/500/1000 trees, depths 4/6/7/8), continuous batching."""
+    import torch
+
+    import paper_2511_09376_gb300 as wdf
+    from paper_2511_09376_gb300 import synth
+    specs = synth.serving_specs()
+    ctx = wdf.ctx_create(0)
+    dev = torch.device("cuda", 0)
+    ens, pools = [], []
+    t0 = time.time()
+    for k, w in enumerate(specs):
+        e_np, _, B = synth.make(w)
+        e = wdf.load_ensemble(ctx, e_np)
+        dB = torch.from_numpy(B).to(dev)
+        wdf.set_background(e, dB, "bf16x3")
+        torch.cuda.synchronize()
+        del dB, B
+        ens.append(e)
+        rng = np.random.default_rng(1000 + k)
+        # request rows and phi in pinned host memory, so the server's copies are asynchronous
+        pool = torch.empty((100_000, w.n_features), dtype=torch.float32).pin_memory().numpy()
+        pool[:] = rng.standard_normal((100_000, w.n_features)).astype(np.float32)
+        pools.append(pool)
+    out_rows = 2_000_000
+    out_pools = [torch.empty((out_rows, w.n_features), dtype=torch.float32).pin_memory().numpy() for w in specs]
+    out_off = [0] * len(specs)
+    setup_s = time.time() - t0
+    srv = wdf.server_create(ctx, ens, device_budget_bytes=16 << 30, n_slots=3, max_wave=32)
+    # warm-up: one request per ensemble
+    for k in range(len(ens)):
+        t, _ = wdf.server_submit(srv, k, pools[k][:1000])
+        wdf.server_wait(srv, t, 600_000)
+    wdf.server_reset_stats(srv)
+    stream = synth.request_stream(synth.SEED_BASE + 5, args.rate, args.duration, len(ens))
+    clocks = ClockSampler(0)
+    clocks.start()
+    tickets = []
+    start = time.perf_counter()
+    offset = [0] * len(ens)
+    for at, k, n in stream:
+        delay = start + at - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        o = offset[k] if offset[k] + n <= 100_000 else 0
+        offset[k] = o + n
+        p = out_off[k] if out_off[k] + n <= out_rows else 0
+        out_off[k] = p + n
+        tickets.append(wdf.server_submit(srv, k, pools[k][o:o + n], phi=out_pools[k][p:p + n])[0])
+    for t in tickets:
+        wdf.server_wait(srv, t, 600_000)
+    wall = time.perf_counter() - start
+    clk = clocks.stop()
+    st = wdf.server_stats(srv)
+    srv.close()
+    offered = sum(n for _, _, n in stream) / args.duration
+    return {
+        "metric": METRIC, "value": st["rows_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(stream), "warmup": 4,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"serving: Poisson {args.rate} req/s for {args.duration} s, rows log-uniform 1-1e5, "
+                               f"ensembles (T,D,F) = {[(w.n_trees, w.depth, w.n_features) for w in specs]}",
+                   "contraction": "bf16x3", "slots": 3, "max_wave": 32, "device_budget_gb": 16},
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "requests": st["completed"],
+        "waves": st["waves"], "offered_rows_per_s": offered, "wall_s": wall, "setup_s": setup_s, "clocks": clk,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,6 +476,8 @@ def main():
     ap.add_argument("--workload", default="large")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
+    ap.add_argument("--duration", type=float, default=30.0, help="serving: seconds of arrivals")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -338,6 +486,12 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args, world, rank)), flush=True)
+        return
+    if args.workload == "ragged":
+        print(json.dumps(run_ragged(args)), flush=True)
+        return
+    if args.workload == "serving":
+        print(json.dumps(run_serving(args)), flush=True)
         return
     if world > 1:
         import torch

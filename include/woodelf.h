@@ -160,6 +160,41 @@ wdf_status wdf_batch_autotune(wdf_batch *batch, int32_t n_requests, const int32_
 wdf_status wdf_batch_tile_rows(const wdf_batch *batch, int32_t depth, int32_t *tile_rows);
 
 /*
+ * Continuous-batching server (project addition).  Requests in host memory queue in
+ * FIFO order; a scheduler thread admits them while one of n_slots execution slots is
+ * free and their device buffers (2 * n * F * 4 bytes) fit in device_budget_bytes, and
+ * runs each admitted wave (up to max_wave_requests requests) as copies in, ONE batch
+ * launch (wdf_batch_explain) and copies out on the slot's stream.  Waves of different
+ * slots overlap on the GPU.  Every ensemble must have its background set and must
+ * outlive the server.  A request's phi equals what wdf_explain gives for the same rows,
+ * whatever shares its wave.
+ * wdf_server_submit: C (n x F, row stride ldc) is read and phi (row stride ldphi)
+ * written asynchronously: both must stay valid until wdf_server_wait / _poll reports the
+ * ticket done.  WDF_ENOMEM if the request alone exceeds the budget, WDF_EBUSY while
+ * shutting down.  wdf_server_wait: WDF_ETIMEOUT if not done within timeout_ms.
+ * wdf_server_stats: latency percentiles are over requests completed since creation or
+ * the last wdf_server_reset_stats, measured from submit to completion; rows_per_s over
+ * the span from the first submit to the last completion.  wdf_server_destroy finishes
+ * every queued request first.
+ */
+typedef struct wdf_server wdf_server;
+typedef struct {
+    int64_t submitted, completed, queued, waves, rows_completed;
+    double p50_ms, p99_ms, max_ms, rows_per_s;
+    int64_t device_bytes_in_use, device_budget;
+} wdf_serving_stats;
+wdf_status wdf_server_create(wdf_ctx *ctx, int32_t n_ensembles, wdf_ensemble *const *ensembles,
+                             int64_t device_budget_bytes, int32_t n_slots, int32_t max_wave_requests,
+                             wdf_server **out);
+wdf_status wdf_server_submit(wdf_server *server, int32_t ensemble_index, const float *C, int64_t n, int64_t ldc,
+                             float *phi, int64_t ldphi, uint64_t *ticket);
+wdf_status wdf_server_wait(wdf_server *server, uint64_t ticket, int64_t timeout_ms);
+wdf_status wdf_server_poll(wdf_server *server, uint64_t ticket, int32_t *done);
+wdf_status wdf_server_stats(wdf_server *server, wdf_serving_stats *out);
+wdf_status wdf_server_reset_stats(wdf_server *server);
+void wdf_server_destroy(wdf_server *server);
+
+/*
  * wdf_global_attribution without any device allocation.  The paper has no counterpart:
  * this is a service for callers that cannot allocate device memory when they need the
  * reduction -- code running under a framework whose caching allocator already holds the

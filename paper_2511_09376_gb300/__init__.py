@@ -17,6 +17,7 @@ from ._binding import (  # noqa: F401
     TF32X3,
     Context,
     Ensemble,
+    Server,
     WdfError,
     ctx_create,
     debug_leaf_hist,
@@ -29,6 +30,12 @@ from ._binding import (  # noqa: F401
     launch_count,
     library_path,
     load_ensemble,
+    server_create,
+    server_poll,
+    server_reset_stats,
+    server_stats,
+    server_submit,
+    server_wait,
     set_background,
     version,
 )

@@ -328,3 +328,89 @@ def batch_tile_rows(batch: Batch, depth: int) -> int:
     v = _c.c_int32(0)
     _check(_lib.wdf_batch_tile_rows(batch.handle, int(depth), _c.byref(v)))
     return int(v.value)
+
+
+_lib.wdf_server_create.argtypes = [_vp, _c.c_int32, _vp, _c.c_int64, _c.c_int32, _c.c_int32, _c.POINTER(_vp)]
+_lib.wdf_server_submit.argtypes = [_vp, _c.c_int32, _vp, _c.c_int64, _c.c_int64, _vp, _c.c_int64,
+                                   _c.POINTER(_c.c_uint64)]
+_lib.wdf_server_wait.argtypes = [_vp, _c.c_uint64, _c.c_int64]
+_lib.wdf_server_poll.argtypes = [_vp, _c.c_uint64, _c.POINTER(_c.c_int32)]
+_lib.wdf_server_stats.argtypes = [_vp, _vp]
+_lib.wdf_server_reset_stats.argtypes = [_vp]
+for _f in ("wdf_server_create", "wdf_server_submit", "wdf_server_wait", "wdf_server_poll", "wdf_server_stats",
+           "wdf_server_reset_stats"):
+    getattr(_lib, _f).restype = _c.c_int
+_lib.wdf_server_destroy.argtypes = [_vp]
+_lib.wdf_server_destroy.restype = None
+
+
+class _ServingStats(_c.Structure):
+    _fields_ = [("submitted", _c.c_int64), ("completed", _c.c_int64), ("queued", _c.c_int64), ("waves", _c.c_int64),
+                ("rows_completed", _c.c_int64), ("p50_ms", _c.c_double), ("p99_ms", _c.c_double),
+                ("max_ms", _c.c_double), ("rows_per_s", _c.c_double), ("device_bytes_in_use", _c.c_int64),
+                ("device_budget", _c.c_int64)]
+
+
+class Server:
+    def __init__(self, ctx, ensembles, handle):
+        self.ctx = ctx
+        self.ensembles = list(ensembles)
+        self.handle = handle
+        self._live = {}  # ticket -> (C, phi) kept alive until the request is done
+
+    def close(self):
+        if self.handle:
+            _lib.wdf_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def server_create(ctx: Context, ensembles, device_budget_bytes: int, n_slots: int = 3, max_wave: int = 32) -> Server:
+    hs = (_vp * len(ensembles))(*[e.handle for e in ensembles])
+    h = _vp()
+    _check(_lib.wdf_server_create(ctx.handle, len(ensembles), hs, int(device_budget_bytes), int(n_slots),
+                                  int(max_wave), _c.byref(h)))
+    return Server(ctx, ensembles, h)
+
+
+def server_submit(server: Server, ensemble_index: int, C, phi=None):
+    """Queue one request (host float32 rows).  Returns (ticket, phi array filled when done)."""
+    C = np.ascontiguousarray(C, dtype=np.float32)
+    F = ensemble_info(server.ensembles[ensemble_index])["n_features"]
+    if phi is None:
+        phi = np.empty((C.shape[0], F), dtype=np.float32)
+    t = _c.c_uint64(0)
+    _check(_lib.wdf_server_submit(server.handle, int(ensemble_index), _vp(C.ctypes.data), int(C.shape[0]),
+                                  int(C.strides[0] // 4), _vp(phi.ctypes.data), int(phi.strides[0] // 4),
+                                  _c.byref(t)))
+    server._live[t.value] = (C, phi)
+    return t.value, phi
+
+
+def server_wait(server: Server, ticket: int, timeout_ms: int = 60_000) -> None:
+    _check(_lib.wdf_server_wait(server.handle, _c.c_uint64(ticket), int(timeout_ms)))
+    server._live.pop(ticket, None)
+
+
+def server_poll(server: Server, ticket: int) -> bool:
+    d = _c.c_int32(0)
+    _check(_lib.wdf_server_poll(server.handle, _c.c_uint64(ticket), _c.byref(d)))
+    if d.value:
+        server._live.pop(ticket, None)
+    return bool(d.value)
+
+
+def server_stats(server: Server) -> dict:
+    st = _ServingStats()
+    _check(_lib.wdf_server_stats(server.handle, _c.byref(st)))
+    return {k: getattr(st, k) for k, _ in _ServingStats._fields_}
+
+
+def server_reset_stats(server: Server) -> None:
+    _check(_lib.wdf_server_reset_stats(server.handle))

@@ -136,7 +136,14 @@ int fill_class(wdf_batch *b, int c, const std::vector<Req> &reqs, int tile_rows)
             items[ni++] = make_int4(b->slot_of[(size_t)r.e], nr, (int)(c0 >> 31), (int)(c0 & 0x7FFFFFFF));
         ++nr;
     }
-    *reinterpret_cast<int *>(b->h_blob + k.off_count) = ni;
+    // longest first: tiles of ensembles with more trees cost more; blocks claim items in
+    // this order, so the cheap ones fill the tail of the launch
+    std::stable_sort(items, items + ni, [&](const int4 &a, const int4 &c) {
+        return b->ens[(size_t)k.members[(size_t)a.x]]->pk.T > b->ens[(size_t)k.members[(size_t)c.x]]->pk.T;
+    });
+    int *hdr = reinterpret_cast<int *>(b->h_blob + k.off_count);
+    hdr[0] = ni;  // item count
+    hdr[1] = 0;   // claim counter, zero at every launch
     return ni;
 }
 
@@ -155,7 +162,7 @@ wdf_status capture(wdf_batch *b) {
                 k.D, reinterpret_cast<const wdf::ExplainJob *>(b->d_blob + k.off_jobs),
                 reinterpret_cast<const wdf::BatchRequest *>(b->d_blob + k.off_reqs),
                 reinterpret_cast<const int4 *>(b->d_blob + k.off_items),
-                reinterpret_cast<const int *>(b->d_blob + k.off_count), k.F_max, k.tile_rows, 0, b->ctx->dev,
+                reinterpret_cast<int *>(b->d_blob + k.off_count), k.F_max, k.tile_rows, 0, b->ctx->dev,
                 b->branch[c]);
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_join[c], b->branch[c]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev_join[c], 0);
@@ -361,11 +368,13 @@ wdf_status wdf_batch_autotune(wdf_batch *b, int32_t n_requests, const int32_t *e
             float ms = 0.0f;
             for (int r = -1; r < reps && e == cudaSuccess; ++r) {  // r = -1 warms up
                 if (r == 0) e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess)  // reset the claim counter of this class
+                    e = cudaMemsetAsync(b->d_blob + k.off_count + sizeof(int), 0, sizeof(int), st);
                 if (e == cudaSuccess)
                     e = wdf::launch_explain_batch(k.D, reinterpret_cast<const wdf::ExplainJob *>(b->d_blob + k.off_jobs),
                                                   reinterpret_cast<const wdf::BatchRequest *>(b->d_blob + k.off_reqs),
                                                   reinterpret_cast<const int4 *>(b->d_blob + k.off_items),
-                                                  reinterpret_cast<const int *>(b->d_blob + k.off_count), k.F_max, tc,
+                                                  reinterpret_cast<int *>(b->d_blob + k.off_count), k.F_max, tc,
                                                   0, b->ctx->dev, st);
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);

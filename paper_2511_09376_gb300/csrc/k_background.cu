@@ -143,26 +143,23 @@ static cudaError_t bg_hist_launch(const float *B, int64_t m, int64_t ldb, int F,
 template <int D, int RT>
 static cudaError_t bg_hist_t(const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T,
                              uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
-    // resident blocks per SM to aim for (shared memory is split between them)
-    int bps = 1;
-    if (const char *env = std::getenv("WDF_BG_BLOCKS_PER_SM")) bps = std::max(1, std::atoi(env));
-    bool agg = false;
-    if (const char *env = std::getenv("WDF_BG_AGG")) agg = std::atoi(env) != 0;
-    const size_t budget = std::min(dev.smem_optin, (size_t)(228 * 1024) / bps - 1024);
+    // One block per SM (measured faster than two, and than match-aggregated increments).
+    // Shared 16-bit counters while the trees fit in at most 8 chunks; beyond that (deep
+    // trees: 64 KB of counters per depth-8 tree) every row tile would be staged once per
+    // chunk, so the counts go straight to global memory and only the node lists are
+    // chunked.
+    const size_t budget = dev.smem_optin;
     int G = std::min(T, 256);
     while (G > 1 && BgLayout<D>(F, RT, G, true).total > budget) --G;
-    const bool smem_hist = BgLayout<D>(F, RT, G, true).total <= budget;
-    if (!smem_hist) {  // counters straight to global memory
-        G = std::min(T, 64);
-        while (G > 1 && BgLayout<D>(F, RT, G, false).total > dev.smem_optin) --G;
+    bool smem_hist = BgLayout<D>(F, RT, G, true).total <= budget && (T + G - 1) / G <= 8;
+    if (!smem_hist) {
+        G = std::min(T, 256);
+        while (G > 1 && BgLayout<D>(F, RT, G, false).total > budget) --G;
     }
     const size_t smem = BgLayout<D>(F, RT, G, smem_hist).total;
     if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
-    if (smem_hist)
-        return agg ? bg_hist_launch<D, RT, true, true>(B, m, ldb, F, ta, T, G, smem, dev, hist, st)
-                   : bg_hist_launch<D, RT, true, false>(B, m, ldb, F, ta, T, G, smem, dev, hist, st);
-    return agg ? bg_hist_launch<D, RT, false, true>(B, m, ldb, F, ta, T, G, smem, dev, hist, st)
-               : bg_hist_launch<D, RT, false, false>(B, m, ldb, F, ta, T, G, smem, dev, hist, st);
+    if (smem_hist) return bg_hist_launch<D, RT, true, false>(B, m, ldb, F, ta, T, G, smem, dev, hist, st);
+    return bg_hist_launch<D, RT, false, false>(B, m, ldb, F, ta, T, G, smem, dev, hist, st);
 }
 
 template <int D>

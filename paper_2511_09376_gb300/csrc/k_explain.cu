@@ -170,16 +170,24 @@ __global__ void __launch_bounds__(TC) k_explain(const float *__restrict__ C, int
     explain_tile<D, TC>(job, C, n, ldc, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
 }
 
-// Persistent form over a ragged batch: work item i is (job, request, first row) and
-// block b takes items b, b + gridDim.x, ...  The item count is read from device memory
-// so one captured graph serves batches of any size up to its capacity.
+// Persistent form over a ragged batch: work item i is (job, request, first row).  Blocks
+// claim items in order from a counter (n_items[1], zero at launch), so expensive items,
+// which the host puts first, spread over the whole grid and cheap ones fill the tail.
+// The item count n_items[0] is read from device memory, so one captured graph serves
+// batches of any size up to its capacity.  Which block computes a tile does not change
+// any row's arithmetic.
 template <int D, int TC>
 __global__ void __launch_bounds__(TC) k_explain_batch(const ExplainJob *__restrict__ jobs,
                                                       const BatchRequest *__restrict__ reqs,
-                                                      const int4 *__restrict__ items, const int *__restrict__ n_items) {
+                                                      const int4 *__restrict__ items, int *__restrict__ n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int count = *n_items;
-    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    __shared__ int claimed;
+    const int count = n_items[0];
+    for (;;) {
+        if (threadIdx.x == 0) claimed = atomicAdd(n_items + 1, 1);
+        __syncthreads();
+        const int i = claimed;
+        if (i >= count) break;
         const int4 it = items[i];
         const ExplainJob job = jobs[it.x];
         const BatchRequest rq = reqs[it.y];
@@ -244,7 +252,7 @@ cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const 
 }
 
 template <int D, int TC>
-static cudaError_t batch_t(const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items, const int *n_items,
+static cudaError_t batch_t(const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items, int *n_items,
                            int F_max, int grid, const DevInfo &dev, cudaStream_t st) {
     const size_t smem = ExLayout<D>(F_max, TC).total;
     if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
@@ -263,7 +271,7 @@ static cudaError_t batch_t(const ExplainJob *jobs, const BatchRequest *reqs, con
 }
 
 template <int D>
-static cudaError_t batch_d(const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items, const int *n_items,
+static cudaError_t batch_d(const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items, int *n_items,
                            int F_max, int tile_rows, int grid, const DevInfo &dev, cudaStream_t st) {
     switch (tile_rows) {
         case 32: return batch_t<D, 32>(jobs, reqs, items, n_items, F_max, grid, dev, st);
@@ -273,7 +281,7 @@ static cudaError_t batch_d(const ExplainJob *jobs, const BatchRequest *reqs, con
 }
 
 cudaError_t launch_explain_batch(int D, const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items,
-                                 const int *n_items, int F_max, int tile_rows, int grid, const DevInfo &dev,
+                                 int *n_items, int F_max, int tile_rows, int grid, const DevInfo &dev,
                                  cudaStream_t st) {
     switch (D) {
         case 2: return batch_d<2>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);

@@ -93,7 +93,7 @@ size_t explain_smem_bytes(int D, int F, int tile_rows);
 // occupancy) walks the work items (job, request, first row split as hi/lo words);
 // *n_items is read on the device.  F_max bounds the feature count of every job.
 cudaError_t launch_explain_batch(int D, const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items,
-                                 const int *n_items, int F_max, int tile_rows, int grid, const DevInfo &dev,
+                                 int *n_items, int F_max, int tile_rows, int grid, const DevInfo &dev,
                                  cudaStream_t st);
 
 // FP64 column means of |phi| and phi: partial sums per row block, then a fixed-order

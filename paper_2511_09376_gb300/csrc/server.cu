@@ -1,0 +1,351 @@
+// Continuous-batching request server over device-resident ensembles.
+//
+// Requests (host buffers) queue in FIFO order.  A scheduler thread admits queued
+// requests while an execution slot is free and their device buffers (consumer rows and
+// phi) fit in the remaining device-memory budget; the admitted requests form one wave:
+// host-to-device copies, ONE batch-graph launch for all of them (wdf_batch_explain, each
+// slot owns its own batch object), device-to-host copies of phi, then an event.  Waves
+// of different slots run concurrently on their own streams, so requests that arrive
+// while others are on the GPU start as soon as a slot and memory free up.  Completion is
+// detected by polling the slot events; latency is measured from submit to completion.
+// A request's rows are computed by exactly the same per-row code whatever else shares
+// its wave, so its phi does not depend on the mix.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "wdf_objects.h"
+#include "woodelf.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+wdf_status fail(wdf_status s, const std::string &msg) {
+    wdf::set_last_error(msg);
+    return s;
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    int ens = 0;
+    const float *C = nullptr;
+    float *phi = nullptr;
+    int64_t n = 0, ldc = 0, ldp = 0;
+    int F = 0;
+    int64_t bytes = 0;  // device bytes while in flight
+    Clock::time_point t_submit;
+    float *d_C = nullptr, *d_phi = nullptr;
+};
+
+struct Wave {
+    std::vector<Request> reqs;
+    int slot = -1;
+    int64_t bytes = 0;
+};
+
+}  // namespace
+
+struct wdf_server {
+    wdf_ctx *ctx = nullptr;
+    std::vector<wdf_ensemble *> ens;
+    int64_t budget = 0;
+    int max_wave = 0;
+    int n_slots = 0;
+    std::vector<wdf_batch *> batch;  // one per slot
+    std::vector<cudaStream_t> stream;
+    std::vector<cudaEvent_t> done_ev;
+    std::vector<Wave> wave;          // per slot, empty when free
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request> pending;
+    std::map<uint64_t, int> state;  // 0 queued, 1 in flight, 2 done, 3 failed
+    uint64_t next_ticket = 1;
+    int64_t in_use = 0;
+    bool stop = false;
+    std::string error;
+    std::vector<double> lat_ms;
+    int64_t submitted = 0, completed = 0, rows_done = 0, waves = 0;
+    Clock::time_point t_first, t_last;
+    std::thread worker;
+};
+
+namespace {
+
+void run(wdf_server *s);
+
+// Launch one wave on its slot (called by the worker without the lock held).
+cudaError_t launch_wave(wdf_server *s, Wave &w) {
+    cudaStream_t st = s->stream[(size_t)w.slot];
+    std::vector<int32_t> idx;
+    std::vector<const float *> C;
+    std::vector<float *> phi;
+    std::vector<int64_t> n, ldc, ldp;
+    for (Request &r : w.reqs) {
+        const size_t row_bytes = (size_t)r.F * sizeof(float);
+        cudaError_t e = cudaMallocAsync((void **)&r.d_C, r.n * row_bytes, st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&r.d_phi, r.n * row_bytes, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(r.d_C, row_bytes, r.C, (size_t)r.ldc * sizeof(float), row_bytes, (size_t)r.n,
+                                  cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        idx.push_back(r.ens);
+        C.push_back(r.d_C);
+        phi.push_back(r.d_phi);
+        n.push_back(r.n);
+        ldc.push_back(r.F);
+        ldp.push_back(r.F);
+    }
+    const wdf_status bs = wdf_batch_explain(s->batch[(size_t)w.slot], (int32_t)idx.size(), idx.data(), C.data(),
+                                            n.data(), ldc.data(), phi.data(), ldp.data(), st);
+    if (bs != WDF_OK) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->error = wdf_last_error();
+        return cudaErrorUnknown;
+    }
+    for (Request &r : w.reqs) {
+        const size_t row_bytes = (size_t)r.F * sizeof(float);
+        cudaError_t e = cudaMemcpy2DAsync(r.phi, (size_t)r.ldp * sizeof(float), r.d_phi, row_bytes, row_bytes,
+                                          (size_t)r.n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaFreeAsync(r.d_C, st);
+        if (e == cudaSuccess) e = cudaFreeAsync(r.d_phi, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaEventRecord(s->done_ev[(size_t)w.slot], st);
+}
+
+void run(wdf_server *s) {
+    cudaSetDevice(s->ctx->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        // reap finished waves
+        bool any_inflight = false;
+        for (int k = 0; k < s->n_slots; ++k) {
+            Wave &w = s->wave[(size_t)k];
+            if (w.reqs.empty()) continue;
+            const cudaError_t q = cudaEventQuery(s->done_ev[(size_t)k]);
+            if (q == cudaErrorNotReady) {
+                any_inflight = true;
+                continue;
+            }
+            const auto now = Clock::now();
+            for (const Request &r : w.reqs) {
+                s->state[r.ticket] = (q == cudaSuccess) ? 2 : 3;
+                s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r.t_submit).count());
+                s->rows_done += r.n;
+                ++s->completed;
+            }
+            if (q != cudaSuccess) s->error = std::string("wave failed: ") + cudaGetErrorString(q);
+            s->t_last = now;
+            s->in_use -= w.bytes;
+            w = Wave();
+            s->cv_done.notify_all();
+        }
+        // admit queued requests into free slots
+        bool launched = false;
+        for (int k = 0; k < s->n_slots && !s->pending.empty(); ++k) {
+            if (!s->wave[(size_t)k].reqs.empty()) continue;
+            Wave w;
+            w.slot = k;
+            while (!s->pending.empty() && (int)w.reqs.size() < s->max_wave &&
+                   s->in_use + w.bytes + s->pending.front().bytes <= s->budget) {
+                w.bytes += s->pending.front().bytes;
+                w.reqs.push_back(s->pending.front());
+                s->state[s->pending.front().ticket] = 1;
+                s->pending.pop_front();
+            }
+            if (w.reqs.empty()) break;  // the head does not fit until memory frees up
+            s->in_use += w.bytes;
+            ++s->waves;
+            lk.unlock();
+            const cudaError_t e = launch_wave(s, w);
+            lk.lock();
+            if (e != cudaSuccess) {
+                s->error = std::string("launch failed: ") + cudaGetErrorString(e);
+                for (const Request &r : w.reqs) s->state[r.ticket] = 3;
+                s->in_use -= w.bytes;
+                s->cv_done.notify_all();
+                continue;
+            }
+            s->wave[(size_t)k] = std::move(w);
+            launched = true;
+            any_inflight = true;
+        }
+        if (s->stop && s->pending.empty() && !any_inflight) break;
+        if (!launched) {
+            // poll the slot events every 50 us while waves are in flight, else sleep until work arrives
+            if (any_inflight)
+                s->cv_work.wait_for(lk, std::chrono::microseconds(50));
+            else
+                s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        }
+    }
+}
+
+double percentile(std::vector<double> v, double p) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = p * (double)(v.size() - 1);
+    const size_t lo = (size_t)pos;
+    const size_t hi = std::min(lo + 1, v.size() - 1);
+    return v[lo] + (pos - (double)lo) * (v[hi] - v[lo]);
+}
+
+}  // namespace
+
+extern "C" {
+
+wdf_status wdf_server_create(wdf_ctx *ctx, int32_t n_ensembles, wdf_ensemble *const *ensembles,
+                             int64_t device_budget_bytes, int32_t n_slots, int32_t max_wave_requests,
+                             wdf_server **out) {
+    if (!ctx || !out || n_ensembles < 1 || !ensembles || device_budget_bytes <= 0 || n_slots < 1 || n_slots > 16 ||
+        max_wave_requests < 1)
+        return fail(WDF_EINVAL, "bad server arguments");
+    *out = nullptr;
+    for (int i = 0; i < n_ensembles; ++i)
+        if (!ensembles[i] || ensembles[i]->ctx != ctx || !ensembles[i]->has_bg)
+            return fail(WDF_EINVAL, "every ensemble must belong to the context and have a background");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    wdf_server *s = new wdf_server();
+    s->ctx = ctx;
+    s->ens.assign(ensembles, ensembles + n_ensembles);
+    s->budget = device_budget_bytes;
+    s->n_slots = n_slots;
+    s->max_wave = max_wave_requests;
+    s->wave.assign((size_t)n_slots, Wave());
+    wdf_status st = WDF_OK;
+    for (int k = 0; k < n_slots && st == WDF_OK; ++k) {
+        wdf_batch *b = nullptr;
+        st = wdf_batch_create(ctx, n_ensembles, ensembles, &b);
+        if (st != WDF_OK) break;
+        s->batch.push_back(b);
+        cudaStream_t str = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&str, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            st = fail(WDF_ECUDA, "stream or event creation failed");
+            break;
+        }
+        s->stream.push_back(str);
+        s->done_ev.push_back(ev);
+    }
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    if (st != WDF_OK) {
+        for (wdf_batch *b : s->batch) wdf_batch_destroy(b);
+        delete s;
+        return st;
+    }
+    s->worker = std::thread(run, s);
+    *out = s;
+    return WDF_OK;
+}
+
+wdf_status wdf_server_submit(wdf_server *s, int32_t ensemble_index, const float *C, int64_t n, int64_t ldc,
+                             float *phi, int64_t ldphi, uint64_t *ticket) {
+    if (!s || !ticket) return fail(WDF_EINVAL, "null argument");
+    if (ensemble_index < 0 || ensemble_index >= (int32_t)s->ens.size()) return fail(WDF_EINVAL, "ensemble index");
+    const int F = s->ens[(size_t)ensemble_index]->pk.F;
+    if (n < 1 || !C || !phi || ldc < F || ldphi < F) return fail(WDF_EINVAL, "bad request sizes");
+    Request r;
+    r.ens = ensemble_index;
+    r.C = C;
+    r.phi = phi;
+    r.n = n;
+    r.ldc = ldc;
+    r.ldp = ldphi;
+    r.F = F;
+    r.bytes = 2 * n * (int64_t)F * (int64_t)sizeof(float);
+    if (r.bytes > s->budget) return fail(WDF_ENOMEM, "request larger than the server's device-memory budget");
+    r.t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return fail(WDF_EBUSY, "server is shutting down");
+        r.ticket = s->next_ticket++;
+        s->state[r.ticket] = 0;
+        if (s->submitted == 0) s->t_first = r.t_submit;
+        ++s->submitted;
+        s->pending.push_back(r);
+    }
+    s->cv_work.notify_one();
+    *ticket = r.ticket;
+    return WDF_OK;
+}
+
+wdf_status wdf_server_wait(wdf_server *s, uint64_t ticket, int64_t timeout_ms) {
+    if (!s) return fail(WDF_EINVAL, "null server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->state.find(ticket);
+    if (it == s->state.end()) return fail(WDF_EINVAL, "unknown ticket");
+    const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                        [&] { return s->state[ticket] >= 2; });
+    if (!ok) return fail(WDF_ETIMEOUT, "request not finished within the timeout");
+    if (s->state[ticket] == 3) return fail(WDF_ECUDA, s->error);
+    return WDF_OK;
+}
+
+wdf_status wdf_server_poll(wdf_server *s, uint64_t ticket, int32_t *done) {
+    if (!s || !done) return fail(WDF_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->state.find(ticket);
+    if (it == s->state.end()) return fail(WDF_EINVAL, "unknown ticket");
+    *done = it->second >= 2 ? 1 : 0;
+    if (it->second == 3) return fail(WDF_ECUDA, s->error);
+    return WDF_OK;
+}
+
+wdf_status wdf_server_stats(wdf_server *s, wdf_serving_stats *out) {
+    if (!s || !out) return fail(WDF_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->queued = (int64_t)s->pending.size();
+    out->waves = s->waves;
+    out->rows_completed = s->rows_done;
+    out->p50_ms = percentile(s->lat_ms, 0.50);
+    out->p99_ms = percentile(s->lat_ms, 0.99);
+    out->max_ms = s->lat_ms.empty() ? 0.0 : *std::max_element(s->lat_ms.begin(), s->lat_ms.end());
+    const double span = s->completed ? std::chrono::duration<double>(s->t_last - s->t_first).count() : 0.0;
+    out->rows_per_s = span > 0 ? (double)s->rows_done / span : 0.0;
+    out->device_bytes_in_use = s->in_use;
+    out->device_budget = s->budget;
+    return WDF_OK;
+}
+
+wdf_status wdf_server_reset_stats(wdf_server *s) {
+    if (!s) return fail(WDF_EINVAL, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->lat_ms.clear();
+    s->submitted = s->completed = s->rows_done = s->waves = 0;
+    return WDF_OK;
+}
+
+void wdf_server_destroy(wdf_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->ctx->device) cudaSetDevice(s->ctx->device);
+    for (size_t k = 0; k < s->stream.size(); ++k) {
+        cudaStreamSynchronize(s->stream[k]);
+        cudaStreamDestroy(s->stream[k]);
+        cudaEventDestroy(s->done_ev[k]);
+    }
+    for (wdf_batch *b : s->batch) wdf_batch_destroy(b);
+    if (prev >= 0 && prev != s->ctx->device) cudaSetDevice(prev);
+    delete s;
+}
+
+}  // extern "C"

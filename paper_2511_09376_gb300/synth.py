@@ -171,6 +171,50 @@ def make(w: Workload | str, n_consumers: int | None = None, n_background: int | 
     return ens, C, B
 
 
+def _log_uniform(rng, lo, hi):
+    return float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+
+
+def ragged_specs(seed: int = SEED_BASE + 4, count: int = 64):
+    """The ragged batch: `count` ensembles with trees log-uniform in [10, 500], depth
+    uniform in 2..8, features uniform in [20, 300] (71 % Gaussian, the rest integer codes,
+    the KDD mix), consumers log-uniform in [1e3, 2e5] and background rows log-uniform in
+    [1e4, 1e6]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        T = int(round(_log_uniform(rng, 10, 500)))
+        D = int(rng.integers(2, 9))
+        F = int(rng.integers(20, 301))
+        n = int(round(_log_uniform(rng, 1e3, 2e5)))
+        m = int(round(_log_uniform(rng, 1e4, 1e6)))
+        out.append(Workload(f"ragged{i}", seed * 1000 + i, n, m, F, int(round(0.71 * F)), T, D, 0.1, 0.1, False))
+    return out
+
+
+def serving_specs(seed: int = SEED_BASE + 5):
+    """The serving set: four resident ensembles (50, 200, 500, 1000 trees of depths 4, 6, 7,
+    8), features drawn uniformly in [50, 500], 1e6-row backgrounds."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, (T, D) in enumerate([(50, 4), (200, 6), (500, 7), (1000, 8)]):
+        F = int(rng.integers(50, 501))
+        out.append(Workload(f"serve{i}", seed * 1000 + i, 0, 1_000_000, F, int(round(0.71 * F)), T, D, 0.1, 0.1,
+                            False))
+    return out
+
+
+def request_stream(seed: int, rate_per_s: float, duration_s: float, n_ensembles: int, n_lo=1, n_hi=100_000):
+    """Poisson arrivals: (arrival time in s, ensemble index, consumer rows log-uniform)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += float(rng.exponential(1.0 / rate_per_s))
+        if t >= duration_s:
+            return out
+        out.append((t, int(rng.integers(0, n_ensembles)), int(round(_log_uniform(rng, n_lo, n_hi)))))
+
+
 _CHUNK = 1 << 16
 
 
