@@ -56,6 +56,11 @@ typedef enum {
 
 typedef enum { WDF_MEM_HOST = 0, WDF_MEM_DEVICE = 1 } wdf_memkind;
 
+/* Which value of the game is computed (section "Beyond SHAP"): Shapley values
+ * (Formula "shap_simplified_formula") or Banzhaf values (Formula
+ * "banzhaf_simplified_formula"); only the pattern-pair table differs. */
+typedef enum { WDF_SHAPLEY = 0, WDF_BANZHAF = 1 } wdf_metric;
+
 typedef struct wdf_ctx wdf_ctx;
 typedef struct wdf_ensemble wdf_ensemble;
 
@@ -102,6 +107,28 @@ wdf_status wdf_ensemble_info(const wdf_ensemble *ens, wdf_info *out);
  */
 wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, wdf_memkind kind,
                               wdf_precision precision, void *stream);
+
+/*
+ * Path-Dependent values (section "Efficient Path-Dependent SHAP Equation"): the
+ * baseline pattern frequencies come from the nodes' covers (the number of training rows
+ * that reached each node) instead of a background, Eq. "path_dependent_estimation":
+ * f_l[p_b] = product over the path of r_i = cover(n_{i+1}) / cover(n_i) where bit i of
+ * p_b is 1 and of 1 - r_i where it is 0.
+ * wdf_set_covers: one cover per input node, indexed like the arrays of
+ * wdf_load_ensemble (host, copied); WDF_EINVAL if one is negative or not finite.  A
+ * node of zero cover gives its children ratio 0.  Synchronous.
+ * wdf_set_path_dependent: replaces the background state by the path-dependent one
+ * (then wdf_explain gives path-dependent values and wdf_expected_value the expected
+ * output under the covers).  WDF_EINVAL without covers.  Stream-ordered like
+ * wdf_set_background.
+ */
+wdf_status wdf_set_covers(wdf_ensemble *ens, const double *cover);
+wdf_status wdf_set_path_dependent(wdf_ensemble *ens, wdf_precision precision, void *stream);
+
+/* Select Shapley (the default) or Banzhaf values: rebuilds the pattern-pair tables
+ * (Algorithm 2 with the metric's cube formula, section "Beyond SHAP"; Algorithm 3's
+ * function v).  The background must be set again afterwards.  Synchronous. */
+wdf_status wdf_set_metric(wdf_ensemble *ens, wdf_metric metric);
 
 /*
  * phi[c, i] for the n consumer rows C (leading dimension ldc) into phi (leading
@@ -219,15 +246,16 @@ wdf_status wdf_global_attribution_noalloc(int32_t device, const float *phi, int6
  * "bg_shap_derivation" step (d)) of every leaf of the complete depth-D layout, as
  * uint32 [T][2^D][2^D] on the host (out_elems must be >= T * 4^D); leaf q of tree t is
  * the q-th leaf from the left, pattern bits root first.  Synchronous.
- * wdf_debug_shapley_table: the FP64 pattern-pair table of one path shape, built on the
- * device (Algorithm 2 + Formula "shap_simplified_formula", unit leaf weight):
- * out[p_b][k * 2^D + p_c] for path position k, where first[k] is the first path
- * position holding the same feature as position k (first[k] == k for a new feature);
- * the value of a feature is stored at its first position, later ones hold 0.  Host
- * output of 2^D * D * 2^D doubles.  Synchronous.
+ * wdf_debug_pair_table: the FP64 pattern-pair table of one path shape, built on the
+ * device (Algorithm 2 + Formula "shap_simplified_formula" or
+ * "banzhaf_simplified_formula", unit leaf weight): out[p_b][k * 2^D + p_c] for path
+ * position k, where first[k] is the first path position holding the same feature as
+ * position k (first[k] == k for a new feature); the value of a feature is stored at
+ * its first position, later ones hold 0.  Host output of 2^D * D * 2^D doubles.
+ * Synchronous.
  */
 wdf_status wdf_debug_leaf_hist(const wdf_ensemble *ens, uint32_t *out, int64_t out_elems);
-wdf_status wdf_debug_shapley_table(wdf_ctx *ctx, int32_t depth, const int32_t *first, double *out);
+wdf_status wdf_debug_pair_table(wdf_ctx *ctx, int32_t depth, const int32_t *first, wdf_metric metric, double *out);
 
 /* Number of kernels this library has launched in the process so far (all devices).
  * Benchmarks read it before and after a timed region. */

@@ -202,3 +202,50 @@ def path_cube(feats, pc, pb, n_out, metric=SHAPLEY):
     if rc < 0:
         raise ValueError("feature id out of range")
     return bool(rc), out
+
+
+def _cover(ens, cover):
+    cv = np.ascontiguousarray(cover, dtype=np.float64)
+    if cv.shape[0] != ens.n_nodes:
+        raise ValueError("one cover per node")
+    return cv
+
+
+def pd_values_bruteforce(ens, cover, C, metric=SHAPLEY):
+    """O0 of the path-dependent game.  Returns (phi, v_empty per consumer)."""
+    lib = _load()
+    C, n, ldc = _rows(C)
+    F = ens.n_features
+    phi = np.zeros((n, F), dtype=np.float64)
+    vempty = np.zeros(n, dtype=np.float64)
+    cv = _cover(ens, cover)
+    rc = lib.orc_pd_values_bruteforce(*_ens_args(ens), _p(cv), ctypes.c_int32(F), _p(C), ctypes.c_int64(n),
+                                      ctypes.c_int64(ldc), ctypes.c_int32(metric), _p(phi), _p(vempty))
+    if rc:
+        raise RuntimeError("orc_pd_values_bruteforce failed")
+    return phi, vempty
+
+
+def pd_values(ens, cover, C, metric=SHAPLEY):
+    """O2 of the path-dependent game (Eq. path_dependent_estimation).  Returns (phi, base)."""
+    lib = _load()
+    C, n, ldc = _rows(C)
+    F = ens.n_features
+    phi = np.zeros((n, F), dtype=np.float64)
+    base = ctypes.c_double(0.0)
+    cv = _cover(ens, cover)
+    rc = lib.orc_pd_values(*_ens_args(ens), _p(cv), ctypes.c_int32(F), _p(C), ctypes.c_int64(n), ctypes.c_int64(ldc),
+                           ctypes.c_int32(metric), _p(phi), ctypes.byref(base))
+    if rc:
+        raise RuntimeError("orc_pd_values failed")
+    return phi, base.value
+
+
+def pd_freq(ens, cover) -> np.ndarray:
+    """Path-dependent frequencies of every leaf's baseline patterns, leaf_table order."""
+    lib = _load()
+    lib.orc_hist_size.restype = ctypes.c_int64
+    hs = lib.orc_hist_size(*_ens_args(ens))
+    out = np.zeros(hs, dtype=np.float64)
+    lib.orc_pd_freq(*_ens_args(ens), _p(_cover(ens, cover)), _p(out))
+    return out

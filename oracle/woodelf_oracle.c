@@ -26,6 +26,11 @@
  *       background is reduced to exact per-leaf pattern counts vc[l][p_b] computed by
  *       CalcDecisionPatterns (Algorithm 1), then every (consumer pattern, counted
  *       background pattern) cube is valued and weighted by vc/m.
+ * The path-dependent game (covers instead of a background) has the same two ends:
+ *   orc_pd_values_bruteforce -- v_c(S) as the cover-weighted expectation walk for all
+ *       coalitions, then Eq. "s";
+ *   orc_pd_values -- the frequency form of section "Efficient Path-Dependent SHAP
+ *       Equation" (Eq. "path_dependent_estimation") in place of vc/m.
  *
  * Conventions read from the paper:
  *   - split(x) = x[feature] < threshold, strict, True goes left (Def. "decision_tree");
@@ -585,4 +590,162 @@ int orc_base_from_hist(int32_t n_trees, const int64_t *off, const int32_t *feat,
     *out = s / (double)m;
     free_leaves(&ls);
     return 0;
+}
+
+/* ---------------------------------------------------------------- path-dependent */
+
+/* The path-dependent game (section "Feature Importance Using Shapley Values": the cover
+ * of a node, the number of training rows that reached it, stands in for the missing
+ * features): v_c(S) = sum over trees of E(root), where E(leaf) = w_leaf and at an inner
+ * node splitting on feature i, E = E(child c follows) when i is in S, else
+ * cover(left)/cover(node) * E(left) + cover(right)/cover(node) * E(right) (a node of
+ * zero cover contributes 0). */
+static double pd_expect(const ens_t *e, const double *cover, int64_t o, int32_t node, const float *x, uint32_t S) {
+    int64_t g = o + node;
+    if (e->feat[g] < 0) return (double)e->val[g];
+    int32_t f = e->feat[g];
+    if ((S >> f) & 1u) {
+        int32_t nx = split_true(x, f, e->thr[g]) ? e->left[g] : e->right[g];
+        return pd_expect(e, cover, o, nx, x, S);
+    }
+    double cn = cover[g];
+    if (cn <= 0.0) return 0.0;
+    int32_t l = e->left[g], r = e->right[g];
+    return (cover[o + l] / cn) * pd_expect(e, cover, o, l, x, S) + (cover[o + r] / cn) * pd_expect(e, cover, o, r, x, S);
+}
+
+/* O0 for the path-dependent game: v_c(S) for all 2^F coalitions, then Eq. "s" (or the
+ * Banzhaf sum).  vempty[c] = v_c({}). */
+int orc_pd_values_bruteforce(int32_t n_trees, const int64_t *off, const int32_t *feat, const float *thr,
+                             const int32_t *left, const int32_t *right, const float *val, const double *cover,
+                             int32_t F, const float *C, int64_t n, int64_t ldc, int32_t metric, double *phi,
+                             double *vempty) {
+    if (F > 20 || F < 1) return -1;
+    ens_t e = {n_trees, off, feat, thr, left, right, val};
+    const uint32_t NS = 1u << F;
+    int err = 0;
+#pragma omp parallel
+    {
+        double *v = (double *)malloc(sizeof(double) * NS);
+        if (!v) err = 1;
+#pragma omp for schedule(dynamic)
+        for (int64_t c = 0; c < n; ++c) {
+            if (!v) continue;
+            const float *x = C + c * ldc;
+            for (uint32_t S = 0; S < NS; ++S) {
+                double acc = 0.0;
+                for (int t = 0; t < n_trees; ++t) acc += pd_expect(&e, cover, off[t], 0, x, S);
+                v[S] = acc;
+            }
+            for (int i = 0; i < F; ++i) {
+                double acc = 0.0;
+                for (uint32_t S = 0; S < NS; ++S) {
+                    if ((S >> i) & 1u) continue;
+                    int sz = __builtin_popcount(S);
+                    double wt = metric == ORC_SHAPLEY ? 1.0 / ((double)F * (double)binom(F - 1, sz))
+                                                      : 1.0 / ldexp(1.0, F - 1);
+                    acc += wt * (v[S | (1u << i)] - v[S]);
+                }
+                phi[c * F + i] = acc;
+            }
+            vempty[c] = v[0];
+        }
+        free(v);
+    }
+    return err ? -1 : 0;
+}
+
+/* Eq. "path_dependent_estimation": for the leaf with index `leaf` (orc_leaf_table order)
+ * the frequency of every baseline pattern p_b, the product over the path nodes of the
+ * cover ratio r_i = cover(n_{i+1}) / cover(n_i) where bit i of p_b is 1 and of 1 - r_i
+ * where it is 0 (root first, bit D-1-i).  out has 2^depth entries. */
+static void pd_freq_leaf(const ens_t *e, const double *cover, const leaf_t *L, double *out) {
+    const int D = L->depth;
+    const int64_t o = e->off[L->tree];
+    double r[ORC_MAXD];
+    for (int i = 0; i < D; ++i) {
+        int32_t nd = L->path[i];
+        int32_t nx = (i + 1 < D) ? L->path[i + 1] : L->node;
+        double cn = cover[o + nd];
+        r[i] = cn > 0.0 ? cover[o + nx] / cn : 0.0;
+    }
+    for (uint64_t p = 0; p < ((uint64_t)1 << D); ++p) {
+        double f = 1.0;
+        for (int i = 0; i < D; ++i) f *= ((p >> (D - 1 - i)) & 1u) ? r[i] : 1.0 - r[i];
+        out[p] = f;
+    }
+}
+
+int orc_pd_freq(int32_t n_trees, const int64_t *off, const int32_t *feat, const float *thr, const int32_t *left,
+                const int32_t *right, const float *val, const double *cover, double *out) {
+    ens_t e = {n_trees, off, feat, thr, left, right, val};
+    leafset_t ls;
+    if (collect_leaves(&e, &ls)) { free_leaves(&ls); return -1; }
+    for (int64_t i = 0; i < ls.n; ++i) pd_freq_leaf(&e, cover, &ls.v[i], out + ls.v[i].hoff);
+    free_leaves(&ls);
+    return 0;
+}
+
+/* O2 for the path-dependent game: as orc_values_hist with the background frequencies
+ * vc / m replaced by the path-dependent frequencies (section "Efficient Path-Dependent
+ * SHAP Equation").  base = sum_l w_l * f_pd[l][all ones] = v_c({}). */
+int orc_pd_values(int32_t n_trees, const int64_t *off, const int32_t *feat, const float *thr, const int32_t *left,
+                  const int32_t *right, const float *val, const double *cover, int32_t F, const float *C, int64_t n,
+                  int64_t ldc, int32_t metric, double *phi, double *base) {
+    ens_t e = {n_trees, off, feat, thr, left, right, val};
+    leafset_t ls;
+    if (collect_leaves(&e, &ls)) { free_leaves(&ls); return -1; }
+    double *freq = (double *)malloc(sizeof(double) * (size_t)(ls.hist_size > 0 ? ls.hist_size : 1));
+    if (!freq) { free_leaves(&ls); return -1; }
+    double b = 0.0;
+    for (int64_t i = 0; i < ls.n; ++i) {
+        pd_freq_leaf(&e, cover, &ls.v[i], freq + ls.v[i].hoff);
+        b += ls.v[i].w * freq[ls.v[i].hoff + ((int64_t)1 << ls.v[i].depth) - 1];
+    }
+    *base = b;
+    int err = 0;
+#pragma omp parallel
+    {
+        uint64_t *pat = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)ls.max_tree_nodes);
+        int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)ls.max_tree_nodes);
+        if (!pat || !queue) err = 1;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t c = 0; c < n; ++c) {
+            if (!pat || !queue) continue;
+            const float *x = C + c * ldc;
+            double *ph = phi + c * F;
+            for (int i = 0; i < F; ++i) ph[i] = 0.0;
+            int64_t li = 0;
+            for (int t = 0; t < n_trees; ++t) {
+                row_patterns(&e, t, x, pat, queue);
+                for (; li < ls.n && ls.v[li].tree == t; ++li) {
+                    const leaf_t *L = &ls.v[li];
+                    const int D = L->depth;
+                    const uint64_t full = D == 0 ? 0 : (((uint64_t)1 << D) - 1);
+                    const uint64_t pc = pat[L->node];
+                    int32_t pf[ORC_MAXD];
+                    for (int i = 0; i < D; ++i) pf[i] = feat[off[t] + L->path[i]];
+                    for (uint64_t pb = 0; pb <= full; ++pb) {
+                        double fr = freq[L->hoff + (int64_t)pb];
+                        if (fr == 0.0) continue;
+                        if ((pc | pb) != full) continue; /* rule 4 */
+                        int32_t pos[ORC_MAXD], neg[ORC_MAXD], P[ORC_MAXD], N[ORC_MAXD];
+                        int np = 0, nn = 0, a, bb;
+                        for (int i = 0; i < D; ++i) {
+                            int bc = (int)((pc >> (D - 1 - i)) & 1u), bv = (int)((pb >> (D - 1 - i)) & 1u);
+                            if (bc && !bv) pos[np++] = pf[i];
+                            if (!bc && bv) neg[nn++] = pf[i];
+                        }
+                        if (!cube_sets(pos, np, neg, nn, P, &a, N, &bb)) continue;
+                        cube_value(P, a, N, bb, L->w * fr, metric, ph);
+                    }
+                }
+            }
+        }
+        free(pat);
+        free(queue);
+    }
+    free(freq);
+    free_leaves(&ls);
+    return err ? -1 : 0;
 }

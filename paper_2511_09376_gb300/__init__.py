@@ -21,7 +21,7 @@ from ._binding import (  # noqa: F401
     WdfError,
     ctx_create,
     debug_leaf_hist,
-    debug_shapley_table,
+    debug_pair_table,
     ensemble_info,
     expected_value,
     explain,
@@ -37,5 +37,8 @@ from ._binding import (  # noqa: F401
     server_submit,
     server_wait,
     set_background,
+    set_covers,
+    set_path_dependent,
+    set_metric,
     version,
 )

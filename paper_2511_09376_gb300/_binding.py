@@ -16,6 +16,7 @@ _LIB_PATH = os.path.join(_HERE, "libwoodelf.so")
 
 FP32, TF32X3, BF16X3 = 0, 1, 2
 _PRECISION = {"fp32": FP32, "tf32x3": TF32X3, "bf16x3": BF16X3}
+_METRIC = {"shapley": 0, "banzhaf": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
 
 if not os.path.exists(_LIB_PATH):
@@ -42,7 +43,8 @@ for _name, _args in {
     "wdf_batch_explain": [_vp, _c.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "wdf_batch_autotune": [_vp, _c.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _c.c_int32, _c.c_char_p, _vp],
     "wdf_batch_tile_rows": [_vp, _c.c_int32, _c.POINTER(_c.c_int32)],
-    "wdf_debug_shapley_table": [_vp, _c.c_int32, _vp, _vp],
+    "wdf_debug_pair_table": [_vp, _c.c_int32, _vp, _c.c_int, _vp],
+    "wdf_set_metric": [_vp, _c.c_int],
 }.items():
     getattr(_lib, _name).argtypes = _args
     getattr(_lib, _name).restype = _c.c_int
@@ -251,12 +253,17 @@ def debug_leaf_hist(e: Ensemble) -> np.ndarray:
     return out
 
 
-def debug_shapley_table(ctx: Context, first) -> np.ndarray:
+def debug_pair_table(ctx: Context, first, metric="shapley") -> np.ndarray:
     f = np.ascontiguousarray(first, dtype=np.int32)
     D = int(f.shape[0])
     out = np.zeros((1 << D, D << D), dtype=np.float64)
-    _check(_lib.wdf_debug_shapley_table(ctx.handle, D, _vp(f.ctypes.data), _vp(out.ctypes.data)))
+    _check(_lib.wdf_debug_pair_table(ctx.handle, D, _vp(f.ctypes.data), _METRIC[metric], _vp(out.ctypes.data)))
     return out
+
+
+def set_metric(e: Ensemble, metric="shapley") -> None:
+    """'shapley' (default) or 'banzhaf'; the background must be set again afterwards."""
+    _check(_lib.wdf_set_metric(e.handle, _METRIC[metric]))
 
 
 class Batch:
@@ -414,3 +421,21 @@ def server_stats(server: Server) -> dict:
 
 def server_reset_stats(server: Server) -> None:
     _check(_lib.wdf_server_reset_stats(server.handle))
+
+
+_lib.wdf_set_covers.argtypes = [_vp, _vp]
+_lib.wdf_set_covers.restype = _c.c_int
+_lib.wdf_set_path_dependent.argtypes = [_vp, _c.c_int, _vp]
+_lib.wdf_set_path_dependent.restype = _c.c_int
+
+
+def set_covers(e: Ensemble, cover) -> None:
+    """Node covers (one per input node, like the node arrays) for path-dependent values."""
+    cv = np.ascontiguousarray(cover, dtype=np.float64)
+    _check(_lib.wdf_set_covers(e.handle, _vp(cv.ctypes.data)))
+
+
+def set_path_dependent(e: Ensemble, precision="fp32", stream=None) -> None:
+    """Use the covers' path-dependent frequencies instead of a background."""
+    prec = _PRECISION[precision] if isinstance(precision, str) else int(precision)
+    _check(_lib.wdf_set_path_dependent(e.handle, prec, _stream_handle(stream)))

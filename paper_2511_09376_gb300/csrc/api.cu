@@ -83,7 +83,7 @@ void free_ensemble(wdf_ensemble *e) {
     dfree(e->d_nodes); dfree(e->d_live); dfree(e->d_keys); dfree(e->d_group_leaf); dfree(e->d_leaf_row);
     dfree(e->d_w_rows); dfree(e->d_tiles); dfree(e->d_t32);
     dfree(e->d_rn_key); dfree(e->d_rn_thr); dfree(e->d_rn_count); dfree(e->d_pt_mask); dfree(e->d_zero);
-    dfree(e->d_t32t); dfree(e->d_tiles128); dfree(e->d_err);
+    dfree(e->d_t32t); dfree(e->d_tiles128); dfree(e->d_err); dfree(e->d_A); dfree(e->d_ratio);
     dfree(e->d_hist); dfree(e->d_vc); dfree(e->d_scale); dfree(e->d_S); dfree(e->d_sfold); dfree(e->d_base);
     for (int i = 0; i < 2; ++i) {
         dfree(e->d_stage_in[i]);
@@ -145,7 +145,7 @@ wdf_status ensure_tensor_core_state(wdf_ensemble *e) {
         WDF_CUDA(cudaMemcpy(e->d_tiles128, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
     float *scratch = nullptr;
     WDF_CUDA(dalloc(&scratch, (size_t)e->G * K * N, &e->bytes));
-    WDF_CUDA(wdf::launch_tables(p.D, e->d_keys, e->G, scratch, nullptr, t32t, 0));
+    WDF_CUDA(wdf::launch_tables(p.D, e->metric, e->d_keys, e->G, scratch, nullptr, t32t, 0));
     WDF_CUDA(cudaStreamSynchronize(0));
     cudaFree(scratch);
     e->bytes -= (int64_t)((size_t)e->G * K * N * sizeof(float));
@@ -159,6 +159,47 @@ cudaError_t copy_rows(float *dst, int64_t ldd, const float *src, int64_t lds, in
                       cudaMemcpyKind kind, cudaStream_t st) {
     if (ldd == F && lds == F) return cudaMemcpyAsync(dst, src, (size_t)rows * F * 4, kind, st);
     return cudaMemcpy2DAsync(dst, (size_t)ldd * 4, src, (size_t)lds * 4, (size_t)F * 4, (size_t)rows, kind, st);
+}
+
+// Buffers of the consumer-independent half (counts, frequencies, S, folded vectors) and,
+// for the tensor-core precisions, the K-major tables.
+wdf_status ensure_frequency_state(wdf_ensemble *ens, wdf_precision precision) {
+    const wdf::Packed &p = ens->pk;
+    const int K = 1 << p.D, N = p.D << p.D;
+    const size_t hist_n = (size_t)p.T * p.NS * (2 * K);
+    if (!ens->d_hist) {
+        WDF_CUDA(dalloc(&ens->d_hist, hist_n, &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_vc, (size_t)ens->n_live * K, &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_A, (size_t)ens->n_live * K, &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_scale, (size_t)ens->n_live, &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_S, (size_t)ens->n_live * N, &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_sfold, hist_n * wdf::slot_pad(p.D), &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_base, 1, &ens->bytes));
+    }
+    ens->has_bg = 0;
+    if (precision != WDF_FP32) return ensure_tensor_core_state(ens);
+    return WDF_OK;
+}
+
+// Step 3 of Algorithm 3 (S = w * M * f for every live leaf, from the frequencies in d_A
+// and the per-leaf scale) in the requested precision, then the fold of every bottom
+// subtree into the vectors the consumer kernel gathers.
+wdf_status contract_and_fold(wdf_ensemble *ens, wdf_precision precision, cudaStream_t st) {
+    const wdf::Packed &p = ens->pk;
+    if (precision == WDF_FP32) {
+        WDF_CUDA(wdf::launch_contract_fp32(p.D, ens->d_A, ens->d_scale, ens->d_tiles, ens->n_tiles, ens->d_t32,
+                                           ens->d_S, st));
+    } else {
+        WDF_CUDA(wdf::launch_contract_tc(p.D, precision == WDF_BF16X3 ? 1 : 0, ens->d_A, ens->d_scale,
+                                         ens->d_tiles128, ens->n_tiles128, ens->d_t32t, ens->d_S, ens->d_err, st));
+        // a bounded wait inside the kernel that expired is reported here
+        int flag = 0;
+        WDF_CUDA(cudaMemcpyAsync(&flag, ens->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        WDF_CUDA(cudaStreamSynchronize(st));
+        if (flag) return fail(WDF_ETIMEOUT, "tensor-core contraction: an mbarrier wait expired");
+    }
+    WDF_CUDA(wdf::launch_fold(p.D, ens->d_S, ens->d_leaf_row, p.T, ens->d_sfold, st));
+    return WDF_OK;
 }
 
 }  // namespace
@@ -259,7 +300,7 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
         chk(cudaMemset(e->d_zero, 0, 16 * sizeof(float)));
         if (e->n_tiles) chk(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
         // step 2 of Algorithm 3 depends only on the path signatures: build the tables now
-        chk(wdf::launch_tables(p.D, e->d_keys, e->G, e->d_t32, nullptr, nullptr, 0));
+        chk(wdf::launch_tables(p.D, e->metric, e->d_keys, e->G, e->d_t32, nullptr, nullptr, 0));
         chk(cudaStreamSynchronize(0));
     }
     if (ce != cudaSuccess) {
@@ -291,6 +332,26 @@ wdf_status wdf_ensemble_info(const wdf_ensemble *ens, wdf_info *out) {
     return WDF_OK;
 }
 
+wdf_status wdf_set_metric(wdf_ensemble *ens, wdf_metric metric) {
+    if (!ens) return fail(WDF_EINVAL, "ens is null");
+    if (metric != WDF_SHAPLEY && metric != WDF_BANZHAF) return fail(WDF_EINVAL, "unknown metric");
+    if ((int)metric == ens->metric) return WDF_OK;
+    DeviceGuard g(ens->ctx->device);
+    WDF_CUDA(cudaDeviceSynchronize());
+    const wdf::Packed &p = ens->pk;
+    ens->metric = (int)metric;
+    ens->has_bg = 0;  // the folded vectors were built from the other tables
+    WDF_CUDA(wdf::launch_tables(p.D, ens->metric, ens->d_keys, ens->G, ens->d_t32, nullptr, nullptr, 0));
+    if (ens->d_t32t) {  // rebuild the tensor-core copy lazily with the new metric
+        dfree(ens->d_t32t);
+        dfree(ens->d_tiles128);
+        dfree(ens->d_err);
+        ens->n_tiles128 = 0;
+    }
+    WDF_CUDA(cudaStreamSynchronize(0));
+    return WDF_OK;
+}
+
 wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, wdf_memkind kind,
                               wdf_precision precision, void *stream) {
     if (!ens) return fail(WDF_EINVAL, "ens is null");
@@ -304,21 +365,10 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
     DeviceGuard g(ens->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const wdf::Packed &p = ens->pk;
-    const int K = 1 << p.D, N = p.D << p.D;
+    const int K = 1 << p.D;
     const size_t hist_n = (size_t)p.T * p.NS * (2 * K);
-    if (!ens->d_hist) {
-        WDF_CUDA(dalloc(&ens->d_hist, hist_n, &ens->bytes));
-        WDF_CUDA(dalloc(&ens->d_vc, (size_t)ens->n_live * K, &ens->bytes));
-        WDF_CUDA(dalloc(&ens->d_scale, (size_t)ens->n_live, &ens->bytes));
-        WDF_CUDA(dalloc(&ens->d_S, (size_t)ens->n_live * N, &ens->bytes));
-        WDF_CUDA(dalloc(&ens->d_sfold, hist_n * wdf::slot_pad(p.D), &ens->bytes));
-        WDF_CUDA(dalloc(&ens->d_base, 1, &ens->bytes));
-    }
-    ens->has_bg = 0;
-    if (precision != WDF_FP32) {
-        wdf_status s = ensure_tensor_core_state(ens);
-        if (s != WDF_OK) return s;
-    }
+    wdf_status s0 = ensure_frequency_state(ens, precision);
+    if (s0 != WDF_OK) return s0;
     WDF_CUDA(cudaMemsetAsync(ens->d_hist, 0, hist_n * 4, st));
     if (kind == WDF_MEM_DEVICE) {
         WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, p.F, ens->arrays(), p.T, ens->d_hist, ens->ctx->dev, st));
@@ -341,24 +391,49 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
             WDF_CUDA(cudaStreamWaitEvent(st, ens->ev_join[i], 0));
         }
     }
-    WDF_CUDA(wdf::launch_leaf_counts(p.D, ens->d_hist, ens->d_group_leaf, ens->n_live, ens->d_vc, st));
+    WDF_CUDA(wdf::launch_leaf_counts(p.D, ens->d_hist, ens->d_group_leaf, ens->n_live, ens->d_vc, ens->d_A, st));
     WDF_CUDA(wdf::launch_scale(ens->d_w_rows, ens->n_live, m, ens->d_scale, st));
-    WDF_CUDA(wdf::launch_base_value(p.D, ens->d_vc, ens->d_w_rows, ens->n_live, m, ens->d_base, st));
-    if (precision == WDF_FP32) {
-        WDF_CUDA(wdf::launch_contract_fp32(p.D, ens->d_vc, ens->d_scale, ens->d_tiles, ens->n_tiles, ens->d_t32,
-                                           ens->d_S, st));
-    } else {
-        WDF_CUDA(wdf::launch_contract_tc(p.D, precision == WDF_BF16X3 ? 1 : 0, ens->d_vc, ens->d_scale,
-                                         ens->d_tiles128, ens->n_tiles128, ens->d_t32t, ens->d_S, ens->d_err, st));
-        // a bounded wait inside the kernel that expired is reported here
-        int flag = 0;
-        WDF_CUDA(cudaMemcpyAsync(&flag, ens->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        WDF_CUDA(cudaStreamSynchronize(st));
-        if (flag) return fail(WDF_ETIMEOUT, "tensor-core contraction: an mbarrier wait expired");
-    }
-    WDF_CUDA(wdf::launch_fold(p.D, ens->d_S, ens->d_leaf_row, p.T, ens->d_sfold, st));
+    WDF_CUDA(wdf::launch_base_value(p.D, ens->d_vc, nullptr, ens->d_w_rows, ens->n_live, m, ens->d_base, st));
+    wdf_status s1 = contract_and_fold(ens, precision, st);
+    if (s1 != WDF_OK) return s1;
     if (kind == WDF_MEM_HOST) WDF_CUDA(cudaStreamSynchronize(st));
     ens->m = m;
+    ens->pd = 0;
+    ens->has_bg = 1;
+    return WDF_OK;
+}
+
+wdf_status wdf_set_covers(wdf_ensemble *ens, const double *cover) {
+    if (!ens) return fail(WDF_EINVAL, "ens is null");
+    std::vector<double> ratio;
+    std::string err;
+    const int rc = wdf::pd_ratios(ens->pk, cover, &ratio, &err);
+    if (rc) return fail((wdf_status)rc, err);
+    DeviceGuard g(ens->ctx->device);
+    if (!ens->d_ratio) WDF_CUDA(dalloc(&ens->d_ratio, std::max<size_t>(ratio.size(), 1), &ens->bytes));
+    if (!ratio.empty())
+        WDF_CUDA(cudaMemcpy(ens->d_ratio, ratio.data(), ratio.size() * sizeof(double), cudaMemcpyHostToDevice));
+    ens->has_covers = 1;
+    return WDF_OK;
+}
+
+wdf_status wdf_set_path_dependent(wdf_ensemble *ens, wdf_precision precision, void *stream) {
+    if (!ens) return fail(WDF_EINVAL, "ens is null");
+    if (!ens->has_covers) return fail(WDF_EINVAL, "wdf_set_covers must succeed before wdf_set_path_dependent");
+    if (precision != WDF_FP32 && precision != WDF_TF32X3 && precision != WDF_BF16X3)
+        return fail(WDF_EINVAL, "unknown precision");
+    DeviceGuard g(ens->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const wdf::Packed &p = ens->pk;
+    wdf_status s0 = ensure_frequency_state(ens, precision);
+    if (s0 != WDF_OK) return s0;
+    WDF_CUDA(wdf::launch_pd_freq(p.D, ens->d_ratio, ens->n_live, ens->d_A, st));
+    WDF_CUDA(wdf::launch_scale(ens->d_w_rows, ens->n_live, 1, ens->d_scale, st));
+    WDF_CUDA(wdf::launch_base_value(p.D, nullptr, ens->d_ratio, ens->d_w_rows, ens->n_live, 1, ens->d_base, st));
+    wdf_status s1 = contract_and_fold(ens, precision, st);
+    if (s1 != WDF_OK) return s1;
+    ens->m = 0;
+    ens->pd = 1;
     ens->has_bg = 1;
     return WDF_OK;
 }
@@ -429,7 +504,7 @@ wdf_status wdf_global_attribution(wdf_ctx *ctx, const float *phi, int64_t n, int
 
 wdf_status wdf_debug_leaf_hist(const wdf_ensemble *ens, uint32_t *out, int64_t out_elems) {
     if (!ens || !out) return fail(WDF_EINVAL, "null argument");
-    if (!ens->has_bg) return fail(WDF_EINVAL, "no background set");
+    if (!ens->has_bg || ens->pd) return fail(WDF_EINVAL, "no background set");
     const wdf::Packed &p = ens->pk;
     const int64_t total = (int64_t)p.T * p.NL * p.NL;
     if (out_elems < total) return fail(WDF_EINVAL, "output too small");
@@ -443,7 +518,7 @@ wdf_status wdf_debug_leaf_hist(const wdf_ensemble *ens, uint32_t *out, int64_t o
     if (ce == cudaSuccess) ce = dalloc(&d_out, (size_t)total, &dummy);
     if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
     if (ce == cudaSuccess) ce = cudaMemcpy(d_all, all.data(), all.size() * 4, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = wdf::launch_leaf_counts(p.D, ens->d_hist, d_all, (int)all.size(), d_out, 0);
+    if (ce == cudaSuccess) ce = wdf::launch_leaf_counts(p.D, ens->d_hist, d_all, (int)all.size(), d_out, nullptr, 0);
     if (ce == cudaSuccess) ce = cudaMemcpy(out, d_out, (size_t)total * 4, cudaMemcpyDeviceToHost);
     dfree(d_all);
     dfree(d_out);
@@ -451,9 +526,10 @@ wdf_status wdf_debug_leaf_hist(const wdf_ensemble *ens, uint32_t *out, int64_t o
     return WDF_OK;
 }
 
-wdf_status wdf_debug_shapley_table(wdf_ctx *ctx, int32_t depth, const int32_t *first, double *out) {
+wdf_status wdf_debug_pair_table(wdf_ctx *ctx, int32_t depth, const int32_t *first, wdf_metric metric, double *out) {
     if (!ctx || !first || !out) return fail(WDF_EINVAL, "null argument");
     if (depth < 1 || depth > wdf::kMaxDepth) return fail(WDF_EINVAL, "depth must be in [1, 8]");
+    if (metric != WDF_SHAPLEY && metric != WDF_BANZHAF) return fail(WDF_EINVAL, "unknown metric");
     uint32_t key = 0;
     for (int k = 0; k < depth; ++k) {
         if (first[k] < 0 || first[k] > k || first[first[k]] != first[k])
@@ -470,7 +546,7 @@ wdf_status wdf_debug_shapley_table(wdf_ctx *ctx, int32_t depth, const int32_t *f
     if (ce == cudaSuccess) ce = dalloc(&d_t32, K * N, &dummy);
     if (ce == cudaSuccess) ce = dalloc(&d_t64, K * N, &dummy);
     if (ce == cudaSuccess) ce = cudaMemcpy(d_key, &key, 4, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = wdf::launch_tables(depth, d_key, 1, d_t32, d_t64, nullptr, 0);
+    if (ce == cudaSuccess) ce = wdf::launch_tables(depth, (int)metric, d_key, 1, d_t32, d_t64, nullptr, 0);
     if (ce == cudaSuccess) ce = cudaMemcpy(out, d_t64, K * N * sizeof(double), cudaMemcpyDeviceToHost);
     dfree(d_key);
     dfree(d_t32);

@@ -189,8 +189,10 @@ cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, int F,
 // vc[row][p] for live leaf row (tree t, leaf q = 4s + j): the leaf pattern p has the
 // subtree-root pattern in its high D-2 bits, then the bit for node r and the bit for
 // the child of r on the path; the decision at the other child of r is summed out.
+// A (when non-null) receives the counts as FP32, the A operand of the contraction
+// (exact below 2^24 background rows).
 __global__ void k_leaf_counts(int D, const uint32_t *__restrict__ hist, const int32_t *__restrict__ group_leaf,
-                              int n_live, uint32_t *__restrict__ vc) {
+                              int n_live, uint32_t *__restrict__ vc, float *__restrict__ A) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)n_live << D;
     if (idx >= total) return;
@@ -212,39 +214,78 @@ __global__ void k_leaf_counts(int D, const uint32_t *__restrict__ hist, const in
         e0 = (pp << 3) | (dn << 2) | 0u | dch;
         e1 = e0 | 2u;
     }
-    vc[idx] = __ldg(h + e0) + __ldg(h + e1);
+    const uint32_t v = __ldg(h + e0) + __ldg(h + e1);
+    vc[idx] = v;
+    if (A) A[idx] = (float)v;
 }
 
 cudaError_t launch_leaf_counts(int D, const uint32_t *hist, const int32_t *group_leaf, int n_live, uint32_t *vc,
-                               cudaStream_t st) {
+                               float *A, cudaStream_t st) {
     const int64_t total = (int64_t)n_live << D;
     if (total == 0) return cudaSuccess;
     const int threads = 256;
-    k_leaf_counts<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(D, hist, group_leaf, n_live, vc);
+    k_leaf_counts<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(D, hist, group_leaf, n_live, vc,
+                                                                                  A);
     count_launches(1);
     return cudaGetLastError();
 }
 
-// E_b f(b): a background row reaches leaf l exactly when its pattern there is all
-// ones, so sum_l w_l * vc[l][all ones] / m.  One block, fixed reduction order.
-__global__ void k_base_value(int D, const uint32_t *__restrict__ vc, const double *__restrict__ w, int n_live,
-                             int64_t m, double *__restrict__ out) {
+// Path-dependent frequencies (Eq. "path_dependent_estimation"): for live leaf row `row`
+// with cover ratios r_k = cover(path node k+1) / cover(path node k), the frequency of
+// baseline pattern p is the product over the path of r_k where bit D-1-k of p is 1 and
+// of 1 - r_k where it is 0, in FP64, stored as the FP32 A operand.
+__global__ void k_pd_freq(int D, const double *__restrict__ ratio, int n_live, float *__restrict__ A) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ((int64_t)n_live << D)) return;
+    const int row = (int)(idx >> D);
+    const uint32_t p = (uint32_t)(idx & ((1 << D) - 1));
+    double f = 1.0;
+    for (int k = 0; k < D; ++k) {
+        const double r = __ldg(ratio + (size_t)row * D + k);
+        f *= ((p >> (D - 1 - k)) & 1u) ? r : 1.0 - r;
+    }
+    A[idx] = (float)f;
+}
+
+cudaError_t launch_pd_freq(int D, const double *ratio, int n_live, float *A, cudaStream_t st) {
+    const int64_t total = (int64_t)n_live << D;
+    if (total == 0) return cudaSuccess;
+    k_pd_freq<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(D, ratio, n_live, A);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// v({}) = sum_l w_l * freq_l(all ones): for the background game freq = vc / m (a row
+// reaches leaf l exactly when its pattern there is all ones, so this is E_b f(b)); for
+// the path-dependent game (ratio non-null) freq = the product of the leaf's cover ratios.
+// One block, fixed reduction order.
+__global__ void k_base_value(int D, const uint32_t *__restrict__ vc, const double *__restrict__ ratio,
+                             const double *__restrict__ w, int n_live, int64_t m, double *__restrict__ out) {
     __shared__ double red[256];
     const int full = (1 << D) - 1;
     double acc = 0.0;
-    for (int r = threadIdx.x; r < n_live; r += blockDim.x) acc += w[r] * (double)vc[((size_t)r << D) + full];
+    for (int r = threadIdx.x; r < n_live; r += blockDim.x) {
+        double f;
+        if (ratio) {
+            f = 1.0;
+            for (int k = 0; k < D; ++k) f *= ratio[(size_t)r * D + k];
+        } else {
+            f = (double)vc[((size_t)r << D) + full] / (double)m;
+        }
+        acc += w[r] * f;
+    }
     red[threadIdx.x] = acc;
     __syncthreads();
     for (int k = 128; k > 0; k >>= 1) {
         if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = red[0] / (double)m;
+    if (threadIdx.x == 0) out[0] = red[0];
 }
 
-cudaError_t launch_base_value(int D, const uint32_t *vc, const double *leaf_w_rows, int n_live, int64_t m,
-                              double *out, cudaStream_t st) {
-    k_base_value<<<1, 256, 0, st>>>(D, vc, leaf_w_rows, n_live, m, out);
+cudaError_t launch_base_value(int D, const uint32_t *vc, const double *ratio, const double *leaf_w_rows, int n_live,
+                              int64_t m, double *out, cudaStream_t st) {
+    k_base_value<<<1, 256, 0, st>>>(D, vc, ratio, leaf_w_rows, n_live, m, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1,10 +1,9 @@
 // Steps 2 and 3 of Algorithm 3: the pattern-pair tables (built once per path
 // signature, section "Algorithmic Improvements" item 2) and their contraction with the
-// background pattern frequencies, s_{l,i} = w_l * M_{l,i} * f_l (Eq.
-// "bg_shap_derivation" step (f)), then the fold of the four leaves of every bottom
-// subtree into the per-entry vectors the consumer kernel gathers.
-#include <cuda_bf16.h>
-
+// baseline pattern frequencies, s_{l,i} = w_l * M_{l,i} * f_l (Eq.
+// "bg_shap_derivation" step (f); f from background counts or, for the path-dependent
+// game, Eq. "path_dependent_estimation"), then the fold of the four leaves of every
+// bottom subtree into the per-entry vectors the consumer kernel gathers.
 #include "launch.h"
 
 namespace wdf {
@@ -17,11 +16,12 @@ __device__ __forceinline__ double binom_small(int n, int k) {
 
 // One thread per (p_b, p_c) of one signature.  The cube of the pair follows the four
 // rules of section "Constructing a WDNF Representation" (root first, bit D-1-k is
-// path position k); its unit-weight Shapley value is Formula "shap_simplified_formula"
-// in FP64 from exact binomials.  A feature met at several path positions is one
+// path position k); its unit-weight value is Formula "shap_simplified_formula" (metric
+// 0, Shapley, in FP64 from exact binomials) or Formula "banzhaf_simplified_formula"
+// (metric 1, Banzhaf: +-1 / 2^(|S|-1)).  A feature met at several path positions is one
 // variable (cubes are sets); its value sits at its first position.
-__global__ void k_tables(int D, const uint32_t *__restrict__ keys, float *__restrict__ t32, double *__restrict__ t64,
-                         float *__restrict__ t32t) {
+__global__ void k_tables(int D, int metric, const uint32_t *__restrict__ keys, float *__restrict__ t32,
+                         double *__restrict__ t64, float *__restrict__ t32t) {
     const int g = blockIdx.y;
     const int K = 1 << D, N = D << D;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -39,8 +39,15 @@ __global__ void k_tables(int D, const uint32_t *__restrict__ keys, float *__rest
     }
     const bool unsat = bottom || (posm & negm);
     const int a = __popc(posm), b = __popc(negm);
-    const double vp = (a > 0) ? 1.0 / ((double)a * binom_small(a + b, a)) : 0.0;
-    const double vn = (b > 0) ? -1.0 / ((double)b * binom_small(a + b, b)) : 0.0;
+    double vp, vn;
+    if (metric == 1) {
+        const double w = (a + b > 0) ? 1.0 / (double)(1u << (a + b - 1)) : 0.0;
+        vp = w;
+        vn = -w;
+    } else {
+        vp = (a > 0) ? 1.0 / ((double)a * binom_small(a + b, a)) : 0.0;
+        vn = (b > 0) ? -1.0 / ((double)b * binom_small(a + b, b)) : 0.0;
+    }
     for (int k = 0; k < D; ++k) {
         double v = 0.0;
         const int f = (key >> (3 * k)) & 7;
@@ -55,47 +62,18 @@ __global__ void k_tables(int D, const uint32_t *__restrict__ keys, float *__rest
     }
 }
 
-cudaError_t launch_tables(int D, const uint32_t *sig_keys, int G, float *t32, double *t64, float *t32t,
+cudaError_t launch_tables(int D, int metric, const uint32_t *sig_keys, int G, float *t32, double *t64, float *t32t,
                           cudaStream_t st) {
     if (G == 0) return cudaSuccess;
     const int total = 1 << (2 * D);
     dim3 grid((total + 255) / 256, G);
-    k_tables<<<grid, 256, 0, st>>>(D, sig_keys, t32, t64, t32t);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-__global__ void k_split(const float *__restrict__ src, int64_t n, int bf16, void *hi, void *lo) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float x = src[i];
-    if (bf16) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-        reinterpret_cast<__nv_bfloat16 *>(hi)[i] = h;
-        reinterpret_cast<__nv_bfloat16 *>(lo)[i] = l;
-    } else {
-        const float h = tf32_round(x);
-        reinterpret_cast<float *>(hi)[i] = h;
-        reinterpret_cast<float *>(lo)[i] = tf32_round(x - h);
-    }
-}
-
-cudaError_t launch_split(const float *src, int64_t n, int bf16, void *hi, void *lo, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    k_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, n, bf16, hi, lo);
+    k_tables<<<grid, 256, 0, st>>>(D, metric, sig_keys, t32, t64, t32t);
     count_launches(1);
     return cudaGetLastError();
 }
 
 // FP32 contraction on CUDA cores: 64 x 64 output tile per block, 4 x 4 per thread.
-__global__ void __launch_bounds__(256) k_contract_fp32(int D, const uint32_t *__restrict__ vc,
+__global__ void __launch_bounds__(256) k_contract_fp32(int D, const float *__restrict__ A,
                                                        const float *__restrict__ scale, const int4 *__restrict__ tiles,
                                                        const float *__restrict__ t32, float *__restrict__ S) {
     constexpr int BM = 64, BN = 64, BK = 16;
@@ -117,7 +95,7 @@ __global__ void __launch_bounds__(256) k_contract_fp32(int D, const uint32_t *__
         for (int i = threadIdx.x; i < BM * BK; i += 256) {
             const int r = i / BK, kk = i % BK;
             const int row = r0 + r, k = k0 + kk;
-            As[kk][r] = (row < r1 && k < K) ? (float)__ldg(vc + ((size_t)row << D) + k) : 0.0f;
+            As[kk][r] = (row < r1 && k < K) ? __ldg(A + ((size_t)row << D) + k) : 0.0f;
         }
         for (int i = threadIdx.x; i < BK * BN; i += 256) {
             const int kk = i / BN, c = i % BN;
@@ -152,12 +130,12 @@ __global__ void __launch_bounds__(256) k_contract_fp32(int D, const uint32_t *__
     }
 }
 
-cudaError_t launch_contract_fp32(int D, const uint32_t *vc, const float *scale, const int4 *tiles, int n_tiles,
+cudaError_t launch_contract_fp32(int D, const float *A, const float *scale, const int4 *tiles, int n_tiles,
                                  const float *t32, float *S, cudaStream_t st) {
     if (n_tiles == 0) return cudaSuccess;
     const int N = D << D;
     dim3 grid(n_tiles, (N + 63) / 64);
-    k_contract_fp32<<<grid, 256, 0, st>>>(D, vc, scale, tiles, t32, S);
+    k_contract_fp32<<<grid, 256, 0, st>>>(D, A, scale, tiles, t32, S);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1,5 +1,5 @@
 // Step 3 of Algorithm 3 on the 5th-generation tensor cores: the stacked contraction
-// S[row][k * 2^D + p_c] = scale[row] * sum_p vc[row][p] * T[g][p][k * 2^D + p_c]
+// S[row][k * 2^D + p_c] = scale[row] * sum_p A[row][p] * T[g][p][k * 2^D + p_c]
 // (Eq. "bg_shap_derivation" step (f) for every leaf of one path signature at once) with
 // split-precision operands: X = X_hi + X_lo, both halves rounded to TF32 (kind::tf32) or
 // BF16 (kind::f16), and three products A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in
@@ -106,7 +106,7 @@ __device__ __forceinline__ void put_split(unsigned char *hi, unsigned char *lo, 
 }  // namespace
 
 template <bool BF16>
-__global__ void __launch_bounds__(128) k_contract_tc(int D, const uint32_t *__restrict__ vc,
+__global__ void __launch_bounds__(128) k_contract_tc(int D, const float *__restrict__ A,
                                                      const float *__restrict__ scale, const int4 *__restrict__ tiles,
                                                      const float *__restrict__ t32t, float *__restrict__ S, int NT,
                                                      int KC, int *__restrict__ err) {
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128) k_contract_tc(int D, const uint32_t *__re
         for (int i = tid; i < kRows * KC; i += 128) {
             const int row = i / KC, k = i % KC;
             const int gr = r0 + row, gk = kc0 + k;
-            const float x = (gr < r1 && gk < K) ? (float)__ldg(vc + ((size_t)gr << D) + gk) : 0.0f;
+            const float x = (gr < r1 && gk < K) ? __ldg(A + ((size_t)gr << D) + gk) : 0.0f;
             put_split<BF16>(a_hi, a_lo, tile_off<EB>(row, k, KC), x);
         }
         for (int i = tid; i < NT * KC; i += 128) {
@@ -224,7 +224,7 @@ size_t contract_tc_smem(int D, int bf16, int *NT, int *KC) {
     return (size_t)2 * (kRows + nt) * kc * eb + 16;
 }
 
-cudaError_t launch_contract_tc(int D, int bf16, const uint32_t *vc, const float *scale, const int4 *tiles, int n_tiles,
+cudaError_t launch_contract_tc(int D, int bf16, const float *A, const float *scale, const int4 *tiles, int n_tiles,
                                const float *t32t, float *S, int *err, cudaStream_t st) {
     if (n_tiles == 0) return cudaSuccess;
     int NT = 0, KC = 0;
@@ -235,11 +235,11 @@ cudaError_t launch_contract_tc(int D, int bf16, const uint32_t *vc, const float 
     if (bf16) {
         e = cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_contract_tc<true><<<grid, 128, smem, st>>>(D, vc, scale, tiles, t32t, S, NT, KC, err);
+        k_contract_tc<true><<<grid, 128, smem, st>>>(D, A, scale, tiles, t32t, S, NT, KC, err);
     } else {
         e = cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_contract_tc<false><<<grid, 128, smem, st>>>(D, vc, scale, tiles, t32t, S, NT, KC, err);
+        k_contract_tc<false><<<grid, 128, smem, st>>>(D, A, scale, tiles, t32t, S, NT, KC, err);
     }
     count_launches(1);
     return cudaGetLastError();

@@ -45,30 +45,31 @@ cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, int F,
                            uint32_t *hist, const DevInfo &dev, cudaStream_t st);
 
 // Per-leaf pattern counts vc[row][p] (u32, 2^D per row) of the live leaves, marginals of
-// the joint entry counts.
+// the joint entry counts; A (nullable) receives them as FP32.
 cudaError_t launch_leaf_counts(int D, const uint32_t *hist, const int32_t *group_leaf, int n_live, uint32_t *vc,
-                               cudaStream_t st);
+                               float *A, cudaStream_t st);
+
+// Path-dependent pattern frequencies A[row][p] (FP32, 2^D per row) from the per-leaf
+// cover ratios ratio[row][k] (FP64, D per row).
+cudaError_t launch_pd_freq(int D, const double *ratio, int n_live, float *A, cudaStream_t st);
 
 // Step 2: FP64 pattern-pair tables of G path signatures; t32 (and t64 when non-null)
 // laid out [G][2^D][D * 2^D]; t32t (when non-null) the K-major copy [G][D * 2^D][2^D].
-cudaError_t launch_tables(int D, const uint32_t *sig_keys, int G, float *t32, double *t64, float *t32t,
+// metric 0: Shapley values, 1: Banzhaf values.
+cudaError_t launch_tables(int D, int metric, const uint32_t *sig_keys, int G, float *t32, double *t64, float *t32t,
                           cudaStream_t st);
 
-// Split copies of the FP32 tables for the tensor-core contraction: hi + lo with hi
-// rounded to TF32 (bf16 == 0) or BF16 (bf16 == 1); n elements.
-cudaError_t launch_split(const float *src, int64_t n, int bf16, void *hi, void *lo, cudaStream_t st);
-
-// Step 3 on CUDA cores: S[row][k * 2^D + p_c] = scale[row] * sum_p vc[row][p] *
-// T[g][p][k * 2^D + p_c] for every live leaf row of group g.  tiles: (group, row0,
-// row_end, 0) work items of up to 64 rows.
-cudaError_t launch_contract_fp32(int D, const uint32_t *vc, const float *scale, const int4 *tiles, int n_tiles,
+// Step 3 on CUDA cores: S[row][k * 2^D + p_c] = scale[row] * sum_p A[row][p] *
+// T[g][p][k * 2^D + p_c] for every live leaf row of group g (A: background counts or
+// path-dependent frequencies).  tiles: (group, row0, row_end, 0) items of up to 64 rows.
+cudaError_t launch_contract_fp32(int D, const float *A, const float *scale, const int4 *tiles, int n_tiles,
                                  const float *t32, float *S, cudaStream_t st);
 
 // Step 3 on the tensor cores (tcgen05, TMEM accumulators): the same S as
 // launch_contract_fp32 from split-precision operands, TF32 (bf16 == 0) or BF16 (1).
 // tiles: (group, row0, row_end, 0) work items of up to 128 rows; t32t the K-major tables.
 // err is set to 1 if a bounded wait expired.
-cudaError_t launch_contract_tc(int D, int bf16, const uint32_t *vc, const float *scale, const int4 *tiles, int n_tiles,
+cudaError_t launch_contract_tc(int D, int bf16, const float *A, const float *scale, const int4 *tiles, int n_tiles,
                                const float *t32t, float *S, int *err, cudaStream_t st);
 
 // Folds the per-leaf S rows of every bottom subtree into per-entry slot vectors
@@ -78,9 +79,10 @@ cudaError_t launch_fold(int D, const float *S, const int32_t *leaf_row, int T, f
 // scale[row] = w[row] / m.
 cudaError_t launch_scale(const double *w, int n_live, int64_t m, float *scale, cudaStream_t st);
 
-// E_b f(b) = (1/m) sum over live leaves of w * vc[all ones] in FP64 (one block).
-cudaError_t launch_base_value(int D, const uint32_t *vc, const double *leaf_w_rows, int n_live, int64_t m,
-                              double *out, cudaStream_t st);
+// v({}) in FP64 (one block): sum over live leaves of w * vc[all ones] / m, or, when
+// ratio is non-null (path-dependent game), of w * (product of the leaf's cover ratios).
+cudaError_t launch_base_value(int D, const uint32_t *vc, const double *ratio, const double *leaf_w_rows, int n_live,
+                              int64_t m, double *out, cudaStream_t st);
 
 // Step 4: phi of n consumer rows, tile_rows consumer rows per block (32, 64 or 128;
 // 0 picks the default for the shared-memory budget).

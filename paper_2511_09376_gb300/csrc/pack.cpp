@@ -27,9 +27,11 @@ struct Src {
 
 // Writes the subtree of input node `node` (local to tree t) at heap position h of
 // depth `depth`; pass-through when node < 0 ("send left") and `keep` says whether the
-// leftmost leaf below keeps output w.
-void place(const Src &s, int t, int32_t node, int h, int depth, float w, bool keep, Packed *p) {
+// leftmost leaf below keeps output w.  csrc: the input node whose cover a pass-through
+// position carries (the pushed-down leaf on the kept path, -1 elsewhere).
+void place(const Src &s, int t, int32_t node, int h, int depth, float w, bool keep, Packed *p, int32_t csrc) {
     const int D = p->D;
+    p->heap_src[(size_t)t * (p->NI + p->NL) + h] = (node >= 0) ? node : csrc;
     if (depth == D) {
         const int q = h - p->NI;
         p->leaf_w[(size_t)t * p->NL + q] = (node >= 0) ? s.val[s.off[t] + node] : (keep ? w : 0.0f);
@@ -40,21 +42,23 @@ void place(const Src &s, int t, int32_t node, int h, int depth, float w, bool ke
         const int64_t g = s.off[t] + node;
         p->node_feat[k] = s.feat[g];
         p->node_thr[k] = s.thr[g];
-        place(s, t, s.left[g], 2 * h + 1, depth + 1, 0.0f, false, p);
-        place(s, t, s.right[g], 2 * h + 2, depth + 1, 0.0f, false, p);
+        place(s, t, s.left[g], 2 * h + 1, depth + 1, 0.0f, false, p, -1);
+        place(s, t, s.right[g], 2 * h + 2, depth + 1, 0.0f, false, p, -1);
         return;
     }
     // an input leaf above depth D, or a node under a pass-through: route every row left
     float wl = w;
     bool kl = keep;
-    if (node >= 0) {  // input leaf: its output moves to the leftmost leaf below
+    int32_t cl = csrc;
+    if (node >= 0) {  // input leaf: its output (and cover) move to the leftmost leaf below
         wl = s.val[s.off[t] + node];
         kl = true;
+        cl = node;
     }
     p->node_feat[k] = p->F;  // virtual column, always 0
     p->node_thr[k] = 1.0f;   // 0 < 1: left
-    place(s, t, -1, 2 * h + 1, depth + 1, wl, kl, p);
-    place(s, t, -1, 2 * h + 2, depth + 1, 0.0f, false, p);
+    place(s, t, -1, 2 * h + 1, depth + 1, wl, kl, p, cl);
+    place(s, t, -1, 2 * h + 2, depth + 1, 0.0f, false, p, -1);
 }
 
 }  // namespace
@@ -132,8 +136,10 @@ int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const f
     p.leaf_w.assign((size_t)T * p.NL, 0.0f);
     p.live.assign((size_t)T, 0);
     p.leaf_row.assign((size_t)T * p.NL, -1);
+    p.heap_src.assign((size_t)T * (p.NI + p.NL), -1);
+    p.in_off.assign(off, off + T + 1);
     Src s{F, off, feat, thr, left, right, val};
-    for (int t = 0; t < T; ++t) place(s, t, 0, 0, 0, 0.0f, false, &p);
+    for (int t = 0; t < T; ++t) place(s, t, 0, 0, 0, 0.0f, false, &p, -1);
 
     // compact lists of the inner nodes that test a real feature
     p.rn_count.assign((size_t)T, 0);
@@ -184,6 +190,40 @@ int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const f
             p.group_leaf.push_back(leaf);
         }
         p.group_off.push_back((int32_t)p.group_leaf.size());
+    }
+    return 0;
+}
+
+int pd_ratios(const Packed &p, const double *cover, std::vector<double> *ratio, std::string *err) {
+    if (!cover) {
+        *err = "cover is null";
+        return 1;
+    }
+    const int64_t total = p.in_off[(size_t)p.T];
+    for (int64_t i = 0; i < total; ++i)
+        if (!(cover[i] >= 0.0) || cover[i] > 1e300) {
+            *err = "covers must be finite and non-negative (node " + std::to_string(i) + ")";
+            return 1;
+        }
+    const int D = p.D;
+    ratio->assign(p.group_leaf.size() * (size_t)D, 0.0);
+    for (size_t row = 0; row < p.group_leaf.size(); ++row) {
+        const int leaf = p.group_leaf[row];
+        const int t = leaf / p.NL, q = leaf % p.NL;
+        auto cov = [&](int h) {
+            const int32_t src = p.heap_src[(size_t)t * (p.NI + p.NL) + h];
+            return src >= 0 ? cover[p.in_off[(size_t)t] + src] : 0.0;
+        };
+        for (int k = 0; k < D; ++k) {
+            const int h = ((p.NL + q) >> (D - k)) - 1;          // path node at depth k
+            const int hn = ((p.NL + q) >> (D - k - 1)) - 1;     // the next one on the path
+            if (p.node_feat[(size_t)t * p.NI + h] == p.F) {      // pass-through: every row goes left
+                (*ratio)[row * D + k] = 1.0;
+                continue;
+            }
+            const double cn = cov(h);
+            (*ratio)[row * D + k] = cn > 0.0 ? cov(hn) / cn : 0.0;
+        }
     }
     return 0;
 }

@@ -44,7 +44,16 @@ struct Packed {
     std::vector<int32_t> group_off;   // [G+1]
     std::vector<int32_t> group_leaf;  // [n_live] t * NL + q, grouped
     std::vector<int32_t> leaf_row;    // [T][NL] row of the leaf in group_leaf, -1 if not live
+    // per tree and complete-layout position (inner nodes then leaves): the local input
+    // node whose cover the position carries, -1 for a zero cover; and the input offsets
+    std::vector<int32_t> heap_src;    // [T][NI + NL]
+    std::vector<int64_t> in_off;      // [T + 1]
 };
+
+// Path-dependent cover ratios of every live leaf row (group_leaf order): ratio[row][k] =
+// cover(path node k+1) / cover(path node k) (0 where the node's cover is 0), from the
+// covers of the input nodes (indexed like the input arrays).  Returns a wdf_status.
+int pd_ratios(const Packed &p, const double *cover, std::vector<double> *ratio, std::string *err);
 
 // Validates and lays out an ensemble; returns a wdf_status value and fills err.
 int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const float *thr, const int32_t *left,

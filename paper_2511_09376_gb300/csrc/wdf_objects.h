@@ -14,6 +14,11 @@ struct wdf_ensemble {
     wdf_ctx *ctx = nullptr;
     wdf::Packed pk;
     int G = 0, n_live = 0, n_tiles = 0;
+    int metric = 0;  // 0 Shapley, 1 Banzhaf (the pattern-pair table formula)
+    int pd = 0;          // 1 when the frequencies are the path-dependent ones
+    int has_covers = 0;  // wdf_set_covers succeeded
+    float *d_A = nullptr;       // frequencies of every live leaf's baseline patterns (FP32)
+    double *d_ratio = nullptr;  // path-dependent cover ratios [live leaves][D]
     int64_t bytes = 0;
     // ensemble (load time)
     int2 *d_nodes = nullptr;

@@ -171,6 +171,30 @@ def make(w: Workload | str, n_consumers: int | None = None, n_background: int | 
     return ens, C, B
 
 
+def node_covers(ens: Ensemble, X: np.ndarray) -> np.ndarray:
+    """Cover of every node: how many rows of X reach it (what a trained model records
+    for its training rows), indexed like the node arrays, as float64."""
+    cover = np.zeros(ens.n_nodes, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    for t in range(ens.n_trees):
+        o = int(ens.tree_offset[t])
+        node = np.zeros(X.shape[0], dtype=np.int64)
+        active = np.ones(X.shape[0], dtype=bool)
+        while active.any():
+            idx = np.nonzero(active)[0]
+            np.add.at(cover, o + node[idx], 1.0)
+            f = ens.feature[o + node[idx]]
+            leaf = f < 0
+            active[idx[leaf]] = False
+            inner = idx[~leaf]
+            if inner.size == 0:
+                break
+            fi = ens.feature[o + node[inner]]
+            go_left = X[inner, fi] < ens.threshold[o + node[inner]]
+            node[inner] = np.where(go_left, ens.left[o + node[inner]], ens.right[o + node[inner]])
+    return cover
+
+
 def _log_uniform(rng, lo, hi):
     return float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
 

@@ -51,3 +51,27 @@ def test_depths_and_precisions(ctx, case, precision):
     bound = ATOL + RTOL * np.abs(want)
     assert (err <= bound).all(), f"{name} {precision}: max |err| {err.max():.3e}, worst excess {(err - bound).max():.3e}"
     e.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_banzhaf_values(ctx, case, precision):
+    """Banzhaf values (Formula banzhaf_simplified_formula in the pattern-pair table)
+    against the oracle's Banzhaf tier."""
+    import torch
+
+    import paper_2511_09376_gb300 as wdf
+    name, ens, C, B, _ = case
+    want = oracle.values_hist(ens, oracle.bg_hist(ens, B), B.shape[0], C, oracle.BANZHAF)
+    e = wdf.load_ensemble(ctx, ens)
+    wdf.set_metric(e, "banzhaf")
+    wdf.set_background(e, torch.from_numpy(B).cuda(), precision)
+    phi = wdf.explain(e, torch.from_numpy(C).cuda()).cpu().numpy().astype(np.float64)
+    err = np.abs(phi - want)
+    bound = ATOL + RTOL * np.abs(want)
+    assert (err <= bound).all(), f"{name} {precision}: max |err| {err.max():.3e}"
+    # switching back to Shapley reproduces the Shapley oracle
+    wdf.set_metric(e, "shapley")
+    wdf.set_background(e, torch.from_numpy(B).cuda(), precision)
+    phi = wdf.explain(e, torch.from_numpy(C).cuda()).cpu().numpy().astype(np.float64)
+    assert (np.abs(phi - case[4]) <= ATOL + RTOL * np.abs(case[4])).all()
+    e.close()

@@ -74,14 +74,15 @@ def _heap_positions(ens, t):
     [0, 1, 2, 3, 4, 5, 6, 7],
     [0, 1, 1, 3, 0, 5, 6, 3],
 ])
-def test_pattern_pair_table_matches_oracle_exactly(wdf, ctx, first):
+@pytest.mark.parametrize("metric", ["shapley", "banzhaf"])
+def test_pattern_pair_table_matches_oracle_exactly(wdf, ctx, first, metric):
     D = len(first)
-    tab = wdf.debug_shapley_table(ctx, first)
+    tab = wdf.debug_pair_table(ctx, first, metric)
     feats = [100 + f for f in first]  # positions sharing a first position share a feature
     K = 1 << D
     for pb in range(K):
         for pc in range(0, K, max(1, K // 64)):
-            ok, vals = oracle.path_cube(feats, pc, pb, 100 + D)
+            ok, vals = oracle.path_cube(feats, pc, pb, 100 + D, oracle.SHAPLEY if metric == "shapley" else oracle.BANZHAF)
             got = tab[pb, [k * K + pc for k in range(D)]]
             want = np.array([vals[100 + k] if first[k] == k else 0.0 for k in range(D)])
             np.testing.assert_array_equal(got, want)

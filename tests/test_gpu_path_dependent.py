@@ -1,0 +1,78 @@
+"""Path-dependent values on the GPU (covers instead of a background, Eq.
+path_dependent_estimation) against the oracle's path-dependent tier, at the FP32-mode
+tolerance, for several depths and both values (Shapley, Banzhaf)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_09376_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+ATOL, RTOL = 1e-6, 1e-5
+CASES = [("d3", 61, 200, 3000, 12, 8, 25, 3, 0.5, 0.2, False),
+         ("d6", 62, 300, 20000, 127, 90, 40, 6, 0.1, 0.1, False),
+         ("d8", 63, 120, 5000, 40, 30, 10, 8, 0.1, 0.1, False)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2511_09376_gb300 as wdf
+    return wdf.ctx_create(0)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision,metric", [("fp32", "shapley"), ("bf16x3", "shapley"), ("fp32", "banzhaf")])
+def test_path_dependent_against_oracle(ctx, case, precision, metric):
+    import torch
+
+    import paper_2511_09376_gb300 as wdf
+    name, seed, n, m, F, ng, T, D, sd, p, comp = case
+    ens, C, B = synth.make(synth.Workload(name, seed, n, m, F, ng, T, D, sd, p, comp))
+    cover = synth.node_covers(ens, B)
+    want, base = oracle.pd_values(ens, cover, C, oracle.SHAPLEY if metric == "shapley" else oracle.BANZHAF)
+    e = wdf.load_ensemble(ctx, ens)
+    if metric != "shapley":
+        wdf.set_metric(e, metric)
+    wdf.set_covers(e, cover)
+    wdf.set_path_dependent(e, precision)
+    phi = wdf.explain(e, torch.from_numpy(C).cuda()).cpu().numpy().astype(np.float64)
+    err = np.abs(phi - want)
+    # A BF16 hi+lo pair carries 16 significant bits: path-dependent frequencies (products
+    # of cover ratios, unlike small background counts) are split with ~2^-17 relative
+    # error, so BF16x3 is held to a tenfold looser bound here.
+    atol, rtol = (10 * ATOL, 10 * RTOL) if precision == "bf16x3" else (ATOL, RTOL)
+    bound = atol + rtol * np.abs(want)
+    assert (err <= bound).all(), f"{name} {precision} {metric}: max |err| {err.max():.3e}"
+    assert wdf.expected_value(e) == pytest.approx(base, rel=1e-9, abs=1e-12)
+    e.close()
+
+
+def test_zero_cover_leaves_above_full_depth(ctx):
+    """Covers from few rows leave nodes and early leaves unreached (cover 0); a leaf pushed
+    down to the full depth must still follow its pass-through nodes with certainty."""
+    import torch
+
+    import paper_2511_09376_gb300 as wdf
+    ens, C, B = synth.make(synth.Workload("z", 64, 200, 3000, 30, 20, 30, 6, 0.1, 0.3, False))
+    cover = synth.node_covers(ens, B[:40])
+    assert (cover == 0).any()
+    want, base = oracle.pd_values(ens, cover, C)
+    e = wdf.load_ensemble(ctx, ens)
+    wdf.set_covers(e, cover)
+    wdf.set_path_dependent(e)
+    phi = wdf.explain(e, torch.from_numpy(C).cuda()).cpu().numpy().astype(np.float64)
+    assert (np.abs(phi - want) <= ATOL + RTOL * np.abs(want)).all()
+    assert wdf.expected_value(e) == pytest.approx(base, rel=1e-9, abs=1e-12)
+
+
+def test_covers_are_validated(ctx):
+    import paper_2511_09376_gb300 as wdf
+    ens, C, B = synth.make("tiny")
+    e = wdf.load_ensemble(ctx, ens)
+    with pytest.raises(wdf.WdfError):
+        wdf.set_path_dependent(e)  # no covers yet
+    bad = synth.node_covers(ens, B)
+    bad[3] = -1.0
+    with pytest.raises(wdf.WdfError):
+        wdf.set_covers(e, bad)
