@@ -82,7 +82,7 @@ namespace {
 void free_ensemble(wdf_ensemble *e) {
     dfree(e->d_nodes); dfree(e->d_live); dfree(e->d_keys); dfree(e->d_group_leaf); dfree(e->d_leaf_row);
     dfree(e->d_w_rows); dfree(e->d_tiles); dfree(e->d_t32);
-    dfree(e->d_rn_key); dfree(e->d_rn_thr); dfree(e->d_rn_count); dfree(e->d_pt_mask); dfree(e->d_zero);
+    dfree(e->d_rn_key); dfree(e->d_rn_thr); dfree(e->d_rn_count); dfree(e->d_pt_mask); dfree(e->d_flush_ok); dfree(e->d_zero);
     dfree(e->d_t32t); dfree(e->d_tiles128); dfree(e->d_err); dfree(e->d_A); dfree(e->d_ratio);
     dfree(e->d_hist); dfree(e->d_vc); dfree(e->d_scale); dfree(e->d_S); dfree(e->d_sfold); dfree(e->d_base);
     for (int i = 0; i < 2; ++i) {
@@ -283,6 +283,7 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
     chk(dalloc(&e->d_rn_thr, p.rn_thr.size(), &e->bytes));
     chk(dalloc(&e->d_rn_count, p.rn_count.size(), &e->bytes));
     chk(dalloc(&e->d_pt_mask, p.pt_mask.size(), &e->bytes));
+    chk(dalloc(&e->d_flush_ok, p.flush_ok.size(), &e->bytes));
     chk(dalloc(&e->d_zero, 16, &e->bytes));
     if (ce == cudaSuccess) {
         chk(cudaMemcpy(e->d_nodes, nodes.data(), nodes.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -297,6 +298,7 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
         chk(cudaMemcpy(e->d_rn_thr, p.rn_thr.data(), p.rn_thr.size() * 4, cudaMemcpyHostToDevice));
         chk(cudaMemcpy(e->d_rn_count, p.rn_count.data(), p.rn_count.size() * 4, cudaMemcpyHostToDevice));
         chk(cudaMemcpy(e->d_pt_mask, p.pt_mask.data(), p.pt_mask.size() * 8, cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(e->d_flush_ok, p.flush_ok.data(), p.flush_ok.size() * 4, cudaMemcpyHostToDevice));
         chk(cudaMemset(e->d_zero, 0, 16 * sizeof(float)));
         if (e->n_tiles) chk(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
         // step 2 of Algorithm 3 depends only on the path signatures: build the tables now

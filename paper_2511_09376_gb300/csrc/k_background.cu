@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(RT) k_bg_hist(const float *__restrict__ B, int
     const int g_cnt = min(G, T - t0);
     const int bins = g_cnt * S::NS * S::E;  // 16-bit counters, two per word
     uint32_t *gdst = hist + (size_t)t0 * S::NS * S::E;
-    stage_trees<D>(t0, g_cnt, XS, ta.nodes, ta.rn_key, ta.rn_thr, ta.rn_count, ta.pt_mask, ta.live, srn, nullptr,
-                   smeta, tid, RT);
+    stage_trees<D>(t0, g_cnt, XS, ta.nodes, ta.rn_key, ta.rn_thr, ta.rn_count, ta.pt_mask, ta.live, nullptr, srn,
+                   nullptr, smeta, tid, RT);
     if (SMEM)
         for (int i = tid; i < bins / 2; i += RT) sh[i] = 0u;
     int64_t since_flush = 0;

@@ -1,0 +1,292 @@
+// Consumer side of Algorithm 3, step 4 (Eq. "bg_shap_derivation" step (g)):
+// phi[c, i] = sum over trees and leaves of s_{l,i}[P[l][c]].
+//
+// One thread per consumer row.  The block stages its rows feature-major in shared
+// memory together with a per-row phi accumulator of the same shape, and the real
+// inner nodes of a chunk of trees.  Per tree the thread evaluates those nodes
+// (decision bitmask in registers), forms its entry at every bottom subtree, and
+// gathers one slot vector per subtree from the folded table -- all gathers of a group
+// of subtrees are issued before any is used, so their L2 latency overlaps; a dead
+// subtree reads a zero row instead.  The slots of the nodes above the bottom subtrees
+// accumulate in registers (one per node, the node-level form of the NumPy indexing of
+// section "Algorithmic Improvements" item 6); every node's value is then added into
+// phi[feature of the node] in the fixed flush order of flush_order.h, eight at a time:
+// a batch that repeats no feature reads its eight phi values before writing any, so
+// the shared-memory round trips overlap; any other batch adds one by one.  Pass-through
+// nodes add into a scratch row.  The order of every floating-point addition into a
+// row's phi depends only on the ensemble, never on which rows share a block.
+//
+// The kernels are templates of the depth; every depth is instantiated in its own
+// translation unit so that they compile in parallel.
+#pragma once
+#include <algorithm>
+#include <cstdlib>
+
+#include "flush_order.h"
+#include "launch.h"
+#include "wdf_device.cuh"
+
+namespace wdf {
+
+template <int D>
+struct ExplainCfg {
+    static constexpr int TCH = 8;  // trees per shared-memory chunk
+    // bottom subtrees gathered together: the largest power of two (a divisor of NS) whose
+    // slot vectors fit in 128 registers
+    static constexpr int gs(int g) { return (g > 1 && g * Shape<D>::SP > 128) ? gs(g / 2) : g; }
+    static constexpr int GS = gs(Shape<D>::NS);
+    static_assert(Shape<D>::NS % GS == 0, "gather groups must tile the bottom subtrees");
+    static_assert(GS == Shape<D>::NS || (3 * GS) % 8 == 0, "flush batches must not straddle gather groups");
+};
+
+template <int D>
+struct ExLayout {
+    size_t x, meta, rn, fo, fl, total;
+    static __host__ __device__ size_t up(size_t v) { return (v + 15) & ~(size_t)15; }
+    __host__ __device__ ExLayout(int F, int TC) {
+        x = up((size_t)(F + 1) * (TC + 1) * 4);  // one of x and phi
+        meta = up((size_t)ExplainCfg<D>::TCH * sizeof(TreeMeta));
+        rn = up((size_t)ExplainCfg<D>::TCH * Shape<D>::NI * sizeof(int2));
+        fo = up((size_t)ExplainCfg<D>::TCH * Shape<D>::NI * sizeof(int));
+        fl = up((size_t)ExplainCfg<D>::TCH * flush_len(D) * sizeof(int));
+        total = 2 * x + meta + rn + fo + fl;
+    }
+};
+
+__device__ __forceinline__ float4 ldg_f4(const float4 *p) {
+    float4 r;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+// One 32-byte entry in a single 256-bit load (the address is 32-byte aligned).
+__device__ __forceinline__ void ldg_f8(const float4 *p, float4 &a, float4 &b) {
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
+// phi[o[q]] += val[q] for the first cnt positions of one flush batch.  fast: the batch
+// repeats no real feature, so all reads may precede all writes.
+__device__ __forceinline__ void flush_batch(float *myphi, const int (&o)[8], const float (&val)[8], int cnt,
+                                            bool fast) {
+    if (fast) {
+        float a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < cnt) a[q] = myphi[o[q]];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < cnt) myphi[o[q]] = a[q] + val[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < cnt) myphi[o[q]] += val[q];
+    }
+}
+
+__device__ __forceinline__ void load_offsets8(const int *p, int (&o)[8]) {
+    const int4 a = *reinterpret_cast<const int4 *>(p), b = *reinterpret_cast<const int4 *>(p + 4);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+
+// One tile of TC consumer rows starting at row c0 of C (n rows), for one ensemble.
+template <int D, int TC>
+__device__ __forceinline__ void explain_tile(const ExplainJob &job, const float *__restrict__ C, int64_t n,
+                                             int64_t ldc, float *__restrict__ phi, int64_t ldp, int64_t c0,
+                                             unsigned char *smem_raw) {
+    using S = Shape<D>;
+    using X = ExplainCfg<D>;
+    constexpr int XS = TC + 1;
+    constexpr int NA = S::NS > 1 ? S::NS - 1 : 1;
+    constexpr int GS = X::GS;
+    constexpr int Q = S::SP / 4;
+    constexpr int FL = flush_len(D), FLB = flush_len_bottom(D);
+    const int F = job.F, T = job.T;
+    const TreeArrays &ta = job.ta;
+    const float *__restrict__ sfold = job.sfold;
+    const ExLayout<D> L(F, TC);
+    float *sx = reinterpret_cast<float *>(smem_raw);
+    float *sp = reinterpret_cast<float *>(smem_raw + L.x);
+    TreeMeta *smeta = reinterpret_cast<TreeMeta *>(smem_raw + 2 * L.x);
+    int2 *srn = reinterpret_cast<int2 *>(smem_raw + 2 * L.x + L.meta);
+    int *sfo = reinterpret_cast<int *>(smem_raw + 2 * L.x + L.meta + L.rn);
+    int *sfl = reinterpret_cast<int *>(smem_raw + 2 * L.x + L.meta + L.rn + L.fo);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int r = warp; r < TC; r += TC / 32) {
+        const int64_t row = c0 + r;
+        const float *src = C + row * ldc;
+        for (int f = lane; f < F; f += 32) sx[f * XS + r] = (row < n) ? __ldg(src + f) : 0.0f;
+    }
+    for (int i = tid; i < (F + 1) * XS; i += TC) sp[i] = 0.0f;
+    sx[F * XS + tid] = 0.0f;
+    float *myphi = sp + tid;
+    const float4 *z4 = reinterpret_cast<const float4 *>(job.zero);
+    for (int tc0 = 0; tc0 < T; tc0 += X::TCH) {
+        const int tcn = min(X::TCH, T - tc0);
+        __syncthreads();
+        stage_trees<D>(tc0, tcn, XS, ta.nodes, ta.rn_key, ta.rn_thr, ta.rn_count, ta.pt_mask, ta.live, ta.flush_ok,
+                       srn, sfo, smeta, tid, TC);
+        __syncthreads();
+        // phi offsets of every tree in flush order (padding writes the scratch row)
+        for (int i = tid; i < tcn * FL; i += TC) {
+            const int g = i / FL, v = flush_node(D, i - g * FL);
+            sfl[i] = v >= 0 ? sfo[g * S::NI + v] : F * XS;
+        }
+        __syncthreads();
+        for (int g = 0; g < tcn; ++g) {
+            const int t = tc0 + g;
+            const TreeMeta &mt = smeta[g];
+            const int *fl = sfl + g * FL;
+            uint64_t dm[S::NW];
+            tree_decisions<D>(srn + g * S::NI, mt, sx, tid, dm);
+            uint32_t ent[S::NS];
+            subtree_entries<D>(dm, ent);
+            const uint64_t lv = mt.live;
+            const uint32_t fok = mt.flush;
+            const float4 *tf = reinterpret_cast<const float4 *>(sfold + (size_t)t * S::NS * S::E * S::SP);
+            float acc[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
+#pragma unroll
+            for (int s0 = 0; s0 < S::NS; s0 += GS) {
+                const uint64_t gmask = (GS >= 64) ? ~0ull : (((1ull << GS) - 1ull) << s0);
+                if (!(lv & gmask)) continue;  // every subtree of the group is dead (warp-uniform)
+                float4 v[GS][Q];
+#pragma unroll
+                for (int j = 0; j < GS; ++j) {
+                    const bool lj = (lv >> (s0 + j)) & 1ull;
+                    const float4 *src = lj ? tf + ((size_t)(s0 + j) * S::E + ent[s0 + j]) * Q : z4;
+                    if (Q == 2) {
+                        ldg_f8(src, v[j][0], v[j][Q > 1 ? 1 : 0]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < Q; ++k) v[j][k] = ldg_f4(src + k);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < GS; ++j) {
+                    const int r = S::NS - 1 + s0 + j;
+                    const float *vj = reinterpret_cast<const float *>(&v[j][0]);
+#pragma unroll
+                    for (int k = 0; k < D - 2; ++k) acc[((r + 1) >> (D - 2 - k)) - 1] += vj[k];
+                }
+                // the three inner nodes of each subtree of the group, in flush order
+#pragma unroll
+                for (int i0 = 0; i0 < 3 * GS; i0 += 8) {
+                    const int fb = 3 * s0 + i0;
+                    int o[8];
+                    load_offsets8(fl + fb, o);
+                    float val[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int i = i0 + q;
+                        val[q] = i < 3 * GS ? reinterpret_cast<const float *>(&v[i / 3][0])[D - 2 + i % 3] : 0.0f;
+                    }
+                    flush_batch(myphi, o, val, min(8, 3 * GS - i0), (fok >> (fb >> 3)) & 1u);
+                }
+            }
+            // the nodes above the bottom subtrees
+#pragma unroll
+            for (int u0 = 0; u0 < S::NS - 1; u0 += 8) {
+                int o[8];
+                load_offsets8(fl + FLB + u0, o);
+                float val[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) val[q] = u0 + q < S::NS - 1 ? acc[u0 + q] : 0.0f;
+                flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int r = warp; r < TC; r += TC / 32) {
+        const int64_t row = c0 + r;
+        if (row >= n) break;
+        float *dst = phi + row * ldp;
+        for (int f = lane; f < F; f += 32) dst[f] = sp[f * XS + r];
+    }
+}
+
+// 1 block per SM is enough (shared memory limits residency anyway): the register
+// budget then covers a whole gather group in flight.
+template <int D, int TC>
+__global__ void __launch_bounds__(TC, 1) k_explain(const float *__restrict__ C, int64_t n, int64_t ldc,
+                                                   ExplainJob job, float *__restrict__ phi, int64_t ldp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    explain_tile<D, TC>(job, C, n, ldc, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
+}
+
+// Persistent form over a ragged batch: work item i is (job, request, first row).  Blocks
+// claim items in order from a counter (n_items[1], zero at launch), so expensive items,
+// which the host puts first, spread over the whole grid and cheap ones fill the tail.
+// The item count n_items[0] is read from device memory, so one captured graph serves
+// batches of any size up to its capacity.  Which block computes a tile does not change
+// any row's arithmetic.
+template <int D, int TC>
+__global__ void __launch_bounds__(TC, 1) k_explain_batch(const ExplainJob *__restrict__ jobs,
+                                                         const BatchRequest *__restrict__ reqs,
+                                                         const int4 *__restrict__ items, int *__restrict__ n_items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int claimed;
+    const int count = n_items[0];
+    for (;;) {
+        if (threadIdx.x == 0) claimed = atomicAdd(n_items + 1, 1);
+        __syncthreads();
+        const int i = claimed;
+        if (i >= count) break;
+        const int4 it = items[i];
+        const ExplainJob job = jobs[it.x];
+        const BatchRequest rq = reqs[it.y];
+        const int64_t c0 = ((int64_t)it.z << 31) | (uint32_t)it.w;
+        explain_tile<D, TC>(job, rq.C, rq.n, rq.ldc, rq.phi, rq.ldp, c0, smem_raw);
+        __syncthreads();
+    }
+}
+
+template <int D, int TC>
+cudaError_t explain_t(const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi, int64_t ldp,
+                      const DevInfo &dev, cudaStream_t st) {
+    const size_t smem = ExLayout<D>(job.F, TC).total;
+    if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
+    auto kern = k_explain<D, TC>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int64_t blocks = (n + TC - 1) / TC;
+    kern<<<(unsigned)blocks, TC, smem, st>>>(C, n, ldc, job, phi, ldp);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int D, int TC>
+cudaError_t batch_t(const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items, int *n_items, int F_max,
+                    int grid, const DevInfo &dev, cudaStream_t st) {
+    const size_t smem = ExLayout<D>(F_max, TC).total;
+    if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
+    auto kern = k_explain_batch<D, TC>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    if (grid <= 0) {
+        int per_sm = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC, smem);
+        if (err != cudaSuccess) return err;
+        grid = dev.sms * (per_sm > 0 ? per_sm : 1);
+    }
+    kern<<<grid, TC, smem, st>>>(jobs, reqs, items, n_items);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Explicit instantiation of the kernels of one (depth, tile rows) pair; each pair is
+// compiled in one of the k_explain_d*.cu translation units.
+#define WDF_EXPLAIN_TILE(d, tc, spec)                                                                            \
+    spec template cudaError_t explain_t<d, tc>(const float *, int64_t, int64_t, const ExplainJob &, float *,      \
+                                               int64_t, const DevInfo &, cudaStream_t);                          \
+    spec template cudaError_t batch_t<d, tc>(const ExplainJob *, const BatchRequest *, const int4 *, int *, int,  \
+                                             int, const DevInfo &, cudaStream_t);
+#define WDF_EXPLAIN_DEPTH(d, spec) WDF_EXPLAIN_TILE(d, 32, spec) WDF_EXPLAIN_TILE(d, 64, spec) \
+    WDF_EXPLAIN_TILE(d, 128, spec)
+
+}  // namespace wdf

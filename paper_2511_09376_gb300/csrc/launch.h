@@ -17,6 +17,7 @@ struct TreeArrays {
     const int32_t *rn_count;  // [T]
     const uint64_t *pt_mask;  // [T][4]
     const uint64_t *live;     // [T]
+    const uint32_t *flush_ok; // [T] bit b: consumer flush batch b repeats no feature
 };
 
 // Everything the consumer kernel needs about one ensemble.

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 
+#include "flush_order.h"
 #include "wdf_internal.h"
 
 namespace wdf {
@@ -159,6 +160,22 @@ int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const f
             }
         }
         p.rn_count[(size_t)t] = c;
+    }
+
+    // flush batches of the consumer kernel whose real features are all distinct
+    p.flush_ok.assign((size_t)T, 0u);
+    for (int t = 0; t < T; ++t) {
+        for (int b = 0; b < flush_batches(p.D); ++b) {
+            bool ok = true;
+            for (int i = 8 * b; i < 8 * b + 8 && ok; ++i)
+                for (int j = 8 * b; j < i && ok; ++j) {
+                    const int vi = flush_node(p.D, i), vj = flush_node(p.D, j);
+                    if (vi < 0 || vj < 0) continue;
+                    const int32_t fi = p.node_feat[(size_t)t * p.NI + vi], fj = p.node_feat[(size_t)t * p.NI + vj];
+                    ok = fi == F || fi != fj;  // pass-through nodes all write the scratch row
+                }
+            if (ok) p.flush_ok[(size_t)t] |= 1u << b;
+        }
     }
 
     // live bottom subtrees and signature groups of the live leaves

@@ -31,7 +31,7 @@ struct TreeMeta {
     uint64_t pt[4];  // pass-through bits
     uint64_t live;   // live bottom subtrees
     int cnt;         // real inner nodes
-    int pad;
+    uint32_t flush;  // bit b: consumer flush batch b repeats no real feature
 };
 
 // Stage trees [t0, t0 + tcn) into shared memory (all threads of the block call it).
@@ -39,8 +39,8 @@ template <int D>
 __device__ __forceinline__ void stage_trees(int t0, int tcn, int XS, const int2 *__restrict__ nodes,
                                             const int32_t *__restrict__ rn_key, const float *__restrict__ rn_thr,
                                             const int32_t *__restrict__ rn_count, const uint64_t *__restrict__ pt_mask,
-                                            const uint64_t *__restrict__ live, int2 *srn, int *sfo, TreeMeta *smeta,
-                                            int tid, int nthreads) {
+                                            const uint64_t *__restrict__ live, const uint32_t *__restrict__ flush_ok,
+                                            int2 *srn, int *sfo, TreeMeta *smeta, int tid, int nthreads) {
     constexpr int NI = Shape<D>::NI;
     for (int i = tid; i < tcn * NI; i += nthreads) {
         const size_t gi = (size_t)t0 * NI + i;
@@ -54,7 +54,7 @@ __device__ __forceinline__ void stage_trees(int t0, int tcn, int XS, const int2 
         for (int w = 0; w < 4; ++w) m.pt[w] = __ldg(pt_mask + (size_t)(t0 + i) * 4 + w);
         m.live = __ldg(live + t0 + i);
         m.cnt = __ldg(rn_count + t0 + i);
-        m.pad = 0;
+        m.flush = flush_ok != nullptr ? __ldg(flush_ok + t0 + i) : 0u;
         smeta[i] = m;
     }
 }

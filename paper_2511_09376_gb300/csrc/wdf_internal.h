@@ -39,6 +39,7 @@ struct Packed {
     std::vector<int32_t> rn_key;      // [T][NI]
     std::vector<float> rn_thr;        // [T][NI]
     std::vector<uint64_t> pt_mask;    // [T][4] bit v: inner node v is a pass-through node
+    std::vector<uint32_t> flush_ok;   // [T] bit b: flush batch b repeats no real feature
     // live leaves grouped by path signature (first-occurrence positions)
     std::vector<uint32_t> sig_key;    // [G] 3 bits per path position
     std::vector<int32_t> group_off;   // [G+1]

@@ -33,6 +33,7 @@ struct wdf_ensemble {
     float *d_rn_thr = nullptr;
     int32_t *d_rn_count = nullptr;
     uint64_t *d_pt_mask = nullptr;
+    uint32_t *d_flush_ok = nullptr;
     float *d_zero = nullptr;  // 64 zero bytes: the entry a dead bottom subtree reads
     // tensor-core contraction: K-major tables, 128-row tiles, wait-expiry flag
     float *d_t32t = nullptr;
@@ -40,7 +41,7 @@ struct wdf_ensemble {
     int n_tiles128 = 0;
     int *d_err = nullptr;
     wdf::TreeArrays arrays() const {
-        return wdf::TreeArrays{d_nodes, d_rn_key, d_rn_thr, d_rn_count, d_pt_mask, d_live};
+        return wdf::TreeArrays{d_nodes, d_rn_key, d_rn_thr, d_rn_count, d_pt_mask, d_live, d_flush_ok};
     }
     wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, d_zero, pk.T, pk.F}; }
     // background state (set_background)
