@@ -171,8 +171,8 @@ wdf_status wdf_global_attribution(wdf_ctx *ctx, const float *phi, int64_t n, int
  * wdf_batch_autotune: runs each depth class's kernel on the given requests with every
  * consumer-tile size that fits (32, 64, 128 rows), reps timed runs each, and keeps the
  * fastest per class (phi is written with valid results).  cache_path (nullable): a text
- * file of "depth features_rounded_up_to_32 tile_rows ms" lines read first and appended
- * to.  Synchronous.  wdf_batch_tile_rows reports the tile size of a depth class (-1 if
+ * file of "depth features code_bytes tile_rows ms" lines (features and decision-code
+ * bytes per row of the class, rounded up to 32) read first and appended to.  Synchronous.  wdf_batch_tile_rows reports the tile size of a depth class (-1 if
  * the batch has none).
  */
 typedef struct wdf_batch wdf_batch;

@@ -80,12 +80,13 @@ void set_last_error(const std::string &msg) { g_err = msg; }
 namespace {
 
 void free_ensemble(wdf_ensemble *e) {
-    dfree(e->d_nodes); dfree(e->d_live); dfree(e->d_keys); dfree(e->d_group_leaf); dfree(e->d_leaf_row);
+    dfree(e->d_nodes); dfree(e->d_keys); dfree(e->d_group_leaf); dfree(e->d_leaf_row);
     dfree(e->d_w_rows); dfree(e->d_tiles); dfree(e->d_t32);
-    dfree(e->d_rn_key); dfree(e->d_rn_thr); dfree(e->d_rn_count); dfree(e->d_pt_mask); dfree(e->d_flush_ok); dfree(e->d_zero);
+    dfree(e->d_rec); dfree(e->d_meta); dfree(e->d_cols); dfree(e->d_col_thr); dfree(e->d_zero);
     dfree(e->d_t32t); dfree(e->d_tiles128); dfree(e->d_err); dfree(e->d_A); dfree(e->d_ratio);
     dfree(e->d_hist); dfree(e->d_vc); dfree(e->d_scale); dfree(e->d_S); dfree(e->d_sfold); dfree(e->d_base);
     for (int i = 0; i < 2; ++i) {
+        dfree(e->d_codes[i]);
         dfree(e->d_stage_in[i]);
         dfree(e->d_stage_out[i]);
         if (e->ist[i]) cudaStreamDestroy(e->ist[i]);
@@ -124,6 +125,23 @@ wdf_status ensure_staging(wdf_ensemble *e, int64_t rows, bool out) {
         e->stage_rows = rows;
     }
     (void)out;
+    return WDF_OK;
+}
+
+// Decision-code buffers for background chunks of up to `rows` rows (at most kCodeRows,
+// a multiple of the largest background tile), nbuf of them.
+constexpr int64_t kCodeRows = 1 << 20;
+wdf_status ensure_codes(wdf_ensemble *e, int64_t rows, int nbuf) {
+    const int64_t tile = wdf::kBgMaxTileRows;
+    rows = std::min((rows + tile - 1) / tile * tile, kCodeRows);
+    const size_t xb = e->pk.cols.size() * (size_t)e->pk.code_bytes;
+    if (rows > e->code_rows) {
+        WDF_CUDA(cudaDeviceSynchronize());
+        for (int i = 0; i < 2; ++i) dfree(e->d_codes[i]);
+        e->code_rows = rows;
+    }
+    for (int i = 0; i < nbuf; ++i)
+        if (!e->d_codes[i]) WDF_CUDA(dalloc(&e->d_codes[i], (size_t)e->code_rows * xb, &e->bytes));
     return WDF_OK;
 }
 
@@ -272,33 +290,30 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
     cudaError_t ce = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (ce == cudaSuccess) ce = x; };
     chk(dalloc(&e->d_nodes, nodes.size(), &e->bytes));
-    chk(dalloc(&e->d_live, p.live.size(), &e->bytes));
     chk(dalloc(&e->d_keys, p.sig_key.size(), &e->bytes));
     chk(dalloc(&e->d_group_leaf, p.group_leaf.size(), &e->bytes));
     chk(dalloc(&e->d_leaf_row, p.leaf_row.size(), &e->bytes));
     chk(dalloc(&e->d_w_rows, w_rows.size(), &e->bytes));
     chk(dalloc(&e->d_tiles, tiles.size(), &e->bytes));
     chk(dalloc(&e->d_t32, (size_t)e->G * K * N, &e->bytes));
-    chk(dalloc(&e->d_rn_key, p.rn_key.size(), &e->bytes));
-    chk(dalloc(&e->d_rn_thr, p.rn_thr.size(), &e->bytes));
-    chk(dalloc(&e->d_rn_count, p.rn_count.size(), &e->bytes));
-    chk(dalloc(&e->d_pt_mask, p.pt_mask.size(), &e->bytes));
-    chk(dalloc(&e->d_flush_ok, p.flush_ok.size(), &e->bytes));
+    chk(dalloc(&e->d_rec, p.rec.size(), &e->bytes));
+    chk(dalloc(&e->d_meta, p.meta.size(), &e->bytes));
+    chk(dalloc(&e->d_cols, p.cols.size(), &e->bytes));
+    chk(dalloc(&e->d_col_thr, std::max<size_t>(p.col_thr.size(), 1), &e->bytes));
     chk(dalloc(&e->d_zero, 16, &e->bytes));
     if (ce == cudaSuccess) {
         chk(cudaMemcpy(e->d_nodes, nodes.data(), nodes.size() * sizeof(int2), cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(e->d_live, p.live.data(), p.live.size() * 8, cudaMemcpyHostToDevice));
         if (e->G) chk(cudaMemcpy(e->d_keys, p.sig_key.data(), p.sig_key.size() * 4, cudaMemcpyHostToDevice));
         if (e->n_live) {
             chk(cudaMemcpy(e->d_group_leaf, p.group_leaf.data(), p.group_leaf.size() * 4, cudaMemcpyHostToDevice));
             chk(cudaMemcpy(e->d_w_rows, w_rows.data(), w_rows.size() * 8, cudaMemcpyHostToDevice));
         }
         chk(cudaMemcpy(e->d_leaf_row, p.leaf_row.data(), p.leaf_row.size() * 4, cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(e->d_rn_key, p.rn_key.data(), p.rn_key.size() * 4, cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(e->d_rn_thr, p.rn_thr.data(), p.rn_thr.size() * 4, cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(e->d_rn_count, p.rn_count.data(), p.rn_count.size() * 4, cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(e->d_pt_mask, p.pt_mask.data(), p.pt_mask.size() * 8, cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(e->d_flush_ok, p.flush_ok.data(), p.flush_ok.size() * 4, cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(e->d_rec, p.rec.data(), p.rec.size() * sizeof(wdf::NodeRec), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(e->d_meta, p.meta.data(), p.meta.size() * sizeof(wdf::TreeMeta), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(e->d_cols, p.cols.data(), p.cols.size() * sizeof(wdf::CodeCol), cudaMemcpyHostToDevice));
+        if (!p.col_thr.empty())
+            chk(cudaMemcpy(e->d_col_thr, p.col_thr.data(), p.col_thr.size() * 4, cudaMemcpyHostToDevice));
         chk(cudaMemset(e->d_zero, 0, 16 * sizeof(float)));
         if (e->n_tiles) chk(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
         // step 2 of Algorithm 3 depends only on the path signatures: build the tables now
@@ -373,9 +388,13 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
     if (s0 != WDF_OK) return s0;
     WDF_CUDA(cudaMemsetAsync(ens->d_hist, 0, hist_n * 4, st));
     if (kind == WDF_MEM_DEVICE) {
-        WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, p.F, ens->arrays(), p.T, ens->d_hist, ens->ctx->dev, st));
+        wdf_status s = ensure_codes(ens, m, 1);
+        if (s != WDF_OK) return s;
+        WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, ens->arrays(), p.T, ens->d_codes[0], ens->code_rows, ens->d_hist,
+                                     ens->ctx->dev, st));
     } else {
         wdf_status s = ensure_staging(ens, m, false);
+        if (s == WDF_OK) s = ensure_codes(ens, ens->stage_rows, 2);
         if (s != WDF_OK) return s;
         WDF_CUDA(cudaEventRecord(ens->ev_fork, st));
         for (int i = 0; i < 2; ++i) WDF_CUDA(cudaStreamWaitEvent(ens->ist[i], ens->ev_fork, 0));
@@ -385,8 +404,8 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
             const int b = (int)(chunk & 1);
             WDF_CUDA(copy_rows(ens->d_stage_in[b], p.F, B + r0 * ldb, ldb, rows, p.F, cudaMemcpyHostToDevice,
                                ens->ist[b]));
-            WDF_CUDA(wdf::launch_bg_hist(p.D, ens->d_stage_in[b], rows, p.F, p.F, ens->arrays(), p.T, ens->d_hist,
-                                         ens->ctx->dev, ens->ist[b]));
+            WDF_CUDA(wdf::launch_bg_hist(p.D, ens->d_stage_in[b], rows, p.F, ens->arrays(), p.T, ens->d_codes[b],
+                                         ens->code_rows, ens->d_hist, ens->ctx->dev, ens->ist[b]));
         }
         for (int i = 0; i < 2; ++i) {
             WDF_CUDA(cudaEventRecord(ens->ev_join[i], ens->ist[i]));

@@ -40,7 +40,7 @@ wdf_status fail(wdf_status s, const std::string &msg) {
     } while (0)
 
 struct Cls {
-    int D = 0, F_max = 0, tile_rows = 0;
+    int D = 0, F_max = 0, xb_max = 0, tile_rows = 0;
     std::vector<int> members;  // batch ensemble indices, in job-slot order
     int cap_reqs = 0, cap_items = 0;
     size_t off_jobs = 0, off_reqs = 0, off_items = 0, off_count = 0;
@@ -162,7 +162,7 @@ wdf_status capture(wdf_batch *b) {
                 k.D, reinterpret_cast<const wdf::ExplainJob *>(b->d_blob + k.off_jobs),
                 reinterpret_cast<const wdf::BatchRequest *>(b->d_blob + k.off_reqs),
                 reinterpret_cast<const int4 *>(b->d_blob + k.off_items),
-                reinterpret_cast<int *>(b->d_blob + k.off_count), k.F_max, k.tile_rows, 0, b->ctx->dev,
+                reinterpret_cast<int *>(b->d_blob + k.off_count), k.F_max, k.xb_max, k.tile_rows, 0, b->ctx->dev,
                 b->branch[c]);
         if (e == cudaSuccess) e = cudaEventRecord(b->ev_join[c], b->branch[c]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev_join[c], 0);
@@ -236,6 +236,7 @@ wdf_status wdf_batch_create(wdf_ctx *ctx, int32_t n_ensembles, wdf_ensemble *con
         }
         Cls &k = b->cls[(size_t)c];
         k.F_max = std::max(k.F_max, b->ens[(size_t)i]->pk.F);
+        k.xb_max = std::max(k.xb_max, (int)b->ens[(size_t)i]->pk.cols.size() * b->ens[(size_t)i]->pk.code_bytes);
         b->cls_of[(size_t)i] = c;
         b->slot_of[(size_t)i] = (int)k.members.size();
         k.members.push_back(i);
@@ -247,8 +248,8 @@ wdf_status wdf_batch_create(wdf_ctx *ctx, int32_t n_ensembles, wdf_ensemble *con
     b->ev_join.assign(b->cls.size(), nullptr);
     for (size_t c = 0; c < b->cls.size() && e == cudaSuccess; ++c) {
         Cls &k = b->cls[c];
-        k.tile_rows = wdf::default_tile_rows(k.D, k.F_max, ctx->dev);
-        if (wdf::explain_smem_bytes(k.D, k.F_max, k.tile_rows) > ctx->dev.smem_optin) {
+        k.tile_rows = wdf::default_tile_rows(k.D, k.F_max, k.xb_max, ctx->dev);
+        if (wdf::explain_smem_bytes(k.D, k.F_max, k.xb_max, k.tile_rows) > ctx->dev.smem_optin) {
             e = cudaErrorInvalidConfiguration;
             break;
         }
@@ -323,15 +324,15 @@ wdf_status wdf_batch_autotune(wdf_batch *b, int32_t n_requests, const int32_t *e
     wdf_status s = gather_requests(b, n_requests, ensemble_index, C, n, ldc, phi, ldphi, &reqs);
     if (s != WDF_OK) return s;
     reps = std::max(1, reps);
-    // cached choices: "depth features_rounded tile_rows ms" per line
+    // cached choices: "depth features_rounded code_bytes_rounded tile_rows ms" per line
     std::vector<std::vector<int>> cached;
     if (cache_path) {
         std::ifstream in(cache_path);
         std::string line;
         while (std::getline(in, line)) {
             std::istringstream ls(line);
-            int d, f, t;
-            if (ls >> d >> f >> t) cached.push_back({d, f, t});
+            int d, f, x, t;
+            if (ls >> d >> f >> x >> t) cached.push_back({d, f, x, t});
         }
     }
     int prev = -1;
@@ -351,10 +352,10 @@ wdf_status wdf_batch_autotune(wdf_batch *b, int32_t n_requests, const int32_t *e
     for (size_t c = 0; c < b->cls.size() && s == WDF_OK; ++c) {
         Cls &k = b->cls[c];
         if (need_reqs[c] == 0) continue;
-        const int fkey = (k.F_max + 31) / 32 * 32;
+        const int fkey = (k.F_max + 31) / 32 * 32, xkey = (k.xb_max + 31) / 32 * 32;
         int hit = 0;
         for (const auto &row : cached)
-            if (row[0] == k.D && row[1] == fkey) hit = row[2];
+            if (row[0] == k.D && row[1] == fkey && row[2] == xkey) hit = row[3];
         if (hit) {
             k.tile_rows = hit;
             continue;
@@ -362,7 +363,7 @@ wdf_status wdf_batch_autotune(wdf_batch *b, int32_t n_requests, const int32_t *e
         float best_ms = 1e30f;
         int best = k.tile_rows;
         for (int tc : cand) {
-            if (wdf::explain_smem_bytes(k.D, k.F_max, tc) > b->ctx->dev.smem_optin) continue;
+            if (wdf::explain_smem_bytes(k.D, k.F_max, k.xb_max, tc) > b->ctx->dev.smem_optin) continue;
             fill_class(b, (int)c, reqs, tc);
             cudaError_t e = cudaMemcpyAsync(b->d_blob, b->h_blob, b->blob_bytes, cudaMemcpyHostToDevice, st);
             float ms = 0.0f;
@@ -374,7 +375,7 @@ wdf_status wdf_batch_autotune(wdf_batch *b, int32_t n_requests, const int32_t *e
                     e = wdf::launch_explain_batch(k.D, reinterpret_cast<const wdf::ExplainJob *>(b->d_blob + k.off_jobs),
                                                   reinterpret_cast<const wdf::BatchRequest *>(b->d_blob + k.off_reqs),
                                                   reinterpret_cast<const int4 *>(b->d_blob + k.off_items),
-                                                  reinterpret_cast<int *>(b->d_blob + k.off_count), k.F_max, tc,
+                                                  reinterpret_cast<int *>(b->d_blob + k.off_count), k.F_max, k.xb_max, tc,
                                                   0, b->ctx->dev, st);
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -392,7 +393,7 @@ wdf_status wdf_batch_autotune(wdf_batch *b, int32_t n_requests, const int32_t *e
         }
         if (s != WDF_OK) break;
         k.tile_rows = best;
-        if (log.is_open()) log << k.D << " " << fkey << " " << best << " " << best_ms << "\n";
+        if (log.is_open()) log << k.D << " " << fkey << " " << xkey << " " << best << " " << best_ms << "\n";
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

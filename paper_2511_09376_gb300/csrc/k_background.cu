@@ -9,10 +9,11 @@
 // marginals of these joint counts (the sibling-leaf observation of section
 // "Algorithmic Improvements" item 3, applied two levels up).
 //
-// Work split: the trees are cut into chunks whose counters fit in shared memory as
-// 16-bit halves of 32-bit words; blocks are numbered chunk-fastest, so the blocks that
-// stage the same row tile run at the same time and share it through L2.  A block
-// flushes its 16-bit counters into the global 32-bit counts before any can overflow.
+// Work split: the rows are first encoded to decision codes (tree_layout.h, one pass
+// over B); the trees are cut into chunks whose counters fit in shared memory as 16-bit
+// halves of 32-bit words; blocks are numbered chunk-fastest, so the blocks that stage
+// the same code tile run at the same time and share it through L2.  A block flushes
+// its 16-bit counters into the global 32-bit counts before any can overflow.
 #include <algorithm>
 #include <cstdlib>
 
@@ -21,33 +22,33 @@
 
 namespace wdf {
 
-// Shared memory layout (bytes, 16-aligned pieces): x tile | tree metadata | real-node
-// lists | 16-bit counters.
+// Shared memory layout (bytes, 16-aligned pieces): code tile | tree metadata | node
+// records | 16-bit counters.
 template <int D>
 struct BgLayout {
-    size_t x, meta, rn, hist, total;
+    size_t x, meta, rec, hist, total;
     static __host__ __device__ size_t up(size_t v) { return (v + 15) & ~(size_t)15; }
-    __host__ __device__ BgLayout(int F, int RT, int G, bool smem_hist) {
-        x = up((size_t)(F + 1) * (RT + 1) * 4);
+    __host__ __device__ BgLayout(int xb, int RT, int G, bool smem_hist) {
+        x = up((size_t)RT * xb);
         meta = up((size_t)G * sizeof(TreeMeta));
-        rn = up((size_t)G * Shape<D>::NI * sizeof(int2));
+        rec = up((size_t)G * Shape<D>::NI * sizeof(NodeRec));
         hist = smem_hist ? up((size_t)G * Shape<D>::NS * Shape<D>::E * 2) : 0;
-        total = x + meta + rn + hist;
+        total = x + meta + rec + hist;
     }
 };
 
-template <int D, int RT, bool SMEM, bool AGG>
-__global__ void __launch_bounds__(RT) k_bg_hist(const float *__restrict__ B, int64_t m, int64_t ldb, int F,
-                                                TreeArrays ta, int T, int G, int chunks,
-                                                uint32_t *__restrict__ hist) {
+// codes: rows [0, m) of one encoded chunk, padded to a multiple of RT rows.
+template <int D, int RT, bool SMEM>
+__global__ void __launch_bounds__(RT) k_bg_hist(const unsigned char *__restrict__ codes, int64_t m, TreeArrays ta,
+                                                int T, int G, int chunks, uint32_t *__restrict__ hist) {
     using S = Shape<D>;
-    constexpr int XS = RT + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const BgLayout<D> L(F, RT, G, SMEM);
-    float *sx = reinterpret_cast<float *>(smem_raw);
+    const int cb = ta.code_bytes, xb = ta.n_cols * cb;
+    const BgLayout<D> L(xb, RT, G, SMEM);
+    unsigned char *sx = smem_raw;
     TreeMeta *smeta = reinterpret_cast<TreeMeta *>(smem_raw + L.x);
-    int2 *srn = reinterpret_cast<int2 *>(smem_raw + L.x + L.meta);
-    uint32_t *sh = reinterpret_cast<uint32_t *>(smem_raw + L.x + L.meta + L.rn);
+    int4 *srec = reinterpret_cast<int4 *>(smem_raw + L.x + L.meta);
+    uint32_t *sh = reinterpret_cast<uint32_t *>(smem_raw + L.x + L.meta + L.rec);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int chunk = blockIdx.x % chunks;
     const int slice = blockIdx.x / chunks, nslices = gridDim.x / chunks;
@@ -55,10 +56,11 @@ __global__ void __launch_bounds__(RT) k_bg_hist(const float *__restrict__ B, int
     const int g_cnt = min(G, T - t0);
     const int bins = g_cnt * S::NS * S::E;  // 16-bit counters, two per word
     uint32_t *gdst = hist + (size_t)t0 * S::NS * S::E;
-    stage_trees<D>(t0, g_cnt, XS, ta.nodes, ta.rn_key, ta.rn_thr, ta.rn_count, ta.pt_mask, ta.live, nullptr, srn,
-                   nullptr, smeta, tid, RT);
+    stage_trees<D>(t0, g_cnt, ta.rec, ta.meta, srec, smeta, tid, RT);
     if (SMEM)
         for (int i = tid; i < bins / 2; i += RT) sh[i] = 0u;
+    const CodeReader xr(sx + (size_t)warp * 32 * xb, lane, cb);
+    const int tile16 = RT * xb / 16;
     int64_t since_flush = 0;
     for (int64_t row0 = (int64_t)slice * RT; row0 < m; row0 += (int64_t)nslices * RT) {
         __syncthreads();
@@ -71,43 +73,27 @@ __global__ void __launch_bounds__(RT) k_bg_hist(const float *__restrict__ B, int
             }
             since_flush = 0;
         }
-        for (int r = warp; r < RT; r += RT / 32) {
-            const int64_t row = row0 + r;
-            const float *src = B + row * ldb;
-            for (int f = lane; f < F; f += 32) sx[f * XS + r] = (row < m) ? __ldg(src + f) : 0.0f;
-        }
-        sx[F * XS + tid] = 0.0f;
+        // the tile's RT rows are RT / 32 consecutive code blocks
+        const uint4 *src = reinterpret_cast<const uint4 *>(codes + row0 * xb);
+        for (int i = tid; i < tile16; i += RT) reinterpret_cast<uint4 *>(sx)[i] = __ldg(src + i);
         __syncthreads();
         since_flush += RT;
         const bool valid = row0 + tid < m;
         for (int g = 0; g < g_cnt; ++g) {
             const TreeMeta &mt = smeta[g];
-            uint64_t dm[S::NW];
-            tree_decisions<D>(srn + (size_t)g * S::NI, mt, sx, tid, dm);
+            uint32_t dw[S::NW];
+            tree_decisions<D>(srec + (size_t)g * S::NI, mt, xr, dw);
             uint32_t ent[S::NS];
-            subtree_entries<D>(dm, ent);
+            subtree_entries<D>(dw, ent);
             const uint64_t lv = mt.live;
 #pragma unroll
             for (int s = 0; s < S::NS; ++s) {
-                if ((lv >> s) & 1ull) {  // warp-uniform
+                if (((lv >> s) & 1ull) && valid) {
                     const uint32_t idx = (uint32_t)(g * S::NS + s) * S::E + ent[s];
-                    if (AGG) {
-                        // lanes with the same counter add once, by the lowest such lane
-                        const uint32_t key = valid ? idx : 0xFFFFFFFFu;
-                        const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
-                        if (valid && lane == __ffs(peers) - 1) {
-                            const uint32_t k = (uint32_t)__popc(peers);
-                            if (SMEM)
-                                atomicAdd(sh + (idx >> 1), k << ((idx & 1u) << 4));
-                            else
-                                atomicAdd(gdst + idx, k);
-                        }
-                    } else if (valid) {
-                        if (SMEM)
-                            atomicAdd(sh + (idx >> 1), 1u << ((idx & 1u) << 4));
-                        else
-                            atomicAdd(gdst + idx, 1u);
-                    }
+                    if (SMEM)
+                        atomicAdd(sh + (idx >> 1), 1u << ((idx & 1u) << 4));
+                    else
+                        atomicAdd(gdst + idx, 1u);
                 }
             }
         }
@@ -122,10 +108,25 @@ __global__ void __launch_bounds__(RT) k_bg_hist(const float *__restrict__ B, int
     }
 }
 
-template <int D, int RT, bool SMEM, bool AGG>
-static cudaError_t bg_hist_launch(const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T, int G,
-                                  size_t smem, const DevInfo &dev, uint32_t *hist, cudaStream_t st) {
-    auto kern = k_bg_hist<D, RT, SMEM, AGG>;
+// Tree chunking of one launch: G trees per block with counters in shared memory while
+// the trees fit in at most 16 chunks; beyond that (deep trees: 64 KB of counters per
+// depth-8 tree) the counts go straight to global memory and only the node records are
+// chunked.
+template <int D, int RT>
+static cudaError_t bg_hist_t(const unsigned char *codes, int64_t m, const TreeArrays &ta, int T, uint32_t *hist,
+                             const DevInfo &dev, cudaStream_t st) {
+    const int xb = ta.n_cols * ta.code_bytes;
+    const size_t budget = dev.smem_optin;
+    int G = std::min(T, 256);
+    while (G > 1 && BgLayout<D>(xb, RT, G, true).total > budget) --G;
+    const bool smem_hist = BgLayout<D>(xb, RT, G, true).total <= budget && (T + G - 1) / G <= 16;
+    if (!smem_hist) {
+        G = std::min(T, 256);
+        while (G > 1 && BgLayout<D>(xb, RT, G, false).total > budget) --G;
+    }
+    const size_t smem = BgLayout<D>(xb, RT, G, smem_hist).total;
+    if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
+    auto kern = smem_hist ? k_bg_hist<D, RT, true> : k_bg_hist<D, RT, false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
@@ -135,55 +136,53 @@ static cudaError_t bg_hist_launch(const float *B, int64_t m, int64_t ldb, int F,
     const int chunks = (T + G - 1) / G;
     const int64_t tiles = (m + RT - 1) / RT;
     const int64_t slices = std::max<int64_t>(1, std::min<int64_t>(tiles, ((int64_t)dev.sms * per_sm) / chunks));
-    kern<<<(unsigned)(slices * chunks), RT, smem, st>>>(B, m, ldb, F, ta, T, G, chunks, hist);
+    kern<<<(unsigned)(slices * chunks), RT, smem, st>>>(codes, m, ta, T, G, chunks, hist);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int D, int RT>
-static cudaError_t bg_hist_t(const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T,
-                             uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
-    // One block per SM (measured faster than two, and than match-aggregated increments).
-    // Shared 16-bit counters while the trees fit in at most 8 chunks; beyond that (deep
-    // trees: 64 KB of counters per depth-8 tree) every row tile would be staged once per
-    // chunk, so the counts go straight to global memory and only the node lists are
-    // chunked.
-    const size_t budget = dev.smem_optin;
-    int G = std::min(T, 256);
-    while (G > 1 && BgLayout<D>(F, RT, G, true).total > budget) --G;
-    bool smem_hist = BgLayout<D>(F, RT, G, true).total <= budget && (T + G - 1) / G <= 8;
-    if (!smem_hist) {
-        G = std::min(T, 256);
-        while (G > 1 && BgLayout<D>(F, RT, G, false).total > budget) --G;
-    }
-    const size_t smem = BgLayout<D>(F, RT, G, smem_hist).total;
-    if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
-    if (smem_hist) return bg_hist_launch<D, RT, true, false>(B, m, ldb, F, ta, T, G, smem, dev, hist, st);
-    return bg_hist_launch<D, RT, false, false>(B, m, ldb, F, ta, T, G, smem, dev, hist, st);
+// Rows per block: the largest tile whose codes take at most 30 % of shared memory.
+static int bg_tile_rows(int xb, const DevInfo &dev) {
+    for (int rt = kBgMaxTileRows; rt > 32; rt /= 2)
+        if ((size_t)rt * xb <= dev.smem_optin * 3 / 10) return rt;
+    return 32;
 }
 
 template <int D>
-static cudaError_t bg_hist_d(const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T,
-                             uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
-    // 128 rows per block while a row tile fits comfortably, else smaller tiles
-    if ((size_t)(F + 1) * 129 * 4 <= dev.smem_optin / 3) return bg_hist_t<D, 128>(B, m, ldb, F, ta, T, hist, dev, st);
-    if ((size_t)(F + 1) * 65 * 4 <= dev.smem_optin / 3) return bg_hist_t<D, 64>(B, m, ldb, F, ta, T, hist, dev, st);
-    return bg_hist_t<D, 32>(B, m, ldb, F, ta, T, hist, dev, st);
+static cudaError_t bg_hist_d(const unsigned char *codes, int64_t m, const TreeArrays &ta, int T, uint32_t *hist,
+                             const DevInfo &dev, cudaStream_t st) {
+    switch (bg_tile_rows(ta.n_cols * ta.code_bytes, dev)) {
+        case 512: return bg_hist_t<D, 512>(codes, m, ta, T, hist, dev, st);
+        case 256: return bg_hist_t<D, 256>(codes, m, ta, T, hist, dev, st);
+        case 128: return bg_hist_t<D, 128>(codes, m, ta, T, hist, dev, st);
+        case 64: return bg_hist_t<D, 64>(codes, m, ta, T, hist, dev, st);
+        default: return bg_hist_t<D, 32>(codes, m, ta, T, hist, dev, st);
+    }
 }
 
-cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T,
-                           uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
+cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, const TreeArrays &ta, int T,
+                           unsigned char *codes, int64_t code_rows, uint32_t *hist, const DevInfo &dev,
+                           cudaStream_t st) {
     if (m == 0) return cudaSuccess;
-    switch (D) {
-        case 2: return bg_hist_d<2>(B, m, ldb, F, ta, T, hist, dev, st);
-        case 3: return bg_hist_d<3>(B, m, ldb, F, ta, T, hist, dev, st);
-        case 4: return bg_hist_d<4>(B, m, ldb, F, ta, T, hist, dev, st);
-        case 5: return bg_hist_d<5>(B, m, ldb, F, ta, T, hist, dev, st);
-        case 6: return bg_hist_d<6>(B, m, ldb, F, ta, T, hist, dev, st);
-        case 7: return bg_hist_d<7>(B, m, ldb, F, ta, T, hist, dev, st);
-        case 8: return bg_hist_d<8>(B, m, ldb, F, ta, T, hist, dev, st);
-        default: return cudaErrorInvalidValue;
+    if (code_rows < kBgMaxTileRows || code_rows % kBgMaxTileRows) return cudaErrorInvalidValue;
+    for (int64_t r0 = 0; r0 < m; r0 += code_rows) {
+        const int64_t rows = std::min(code_rows, m - r0);
+        const int64_t rows_pad = (rows + kBgMaxTileRows - 1) / kBgMaxTileRows * kBgMaxTileRows;
+        cudaError_t err = launch_encode_codes(B + r0 * ldb, rows, ldb, ta, rows_pad, codes, dev, st);
+        if (err != cudaSuccess) return err;
+        switch (D) {
+            case 2: err = bg_hist_d<2>(codes, rows, ta, T, hist, dev, st); break;
+            case 3: err = bg_hist_d<3>(codes, rows, ta, T, hist, dev, st); break;
+            case 4: err = bg_hist_d<4>(codes, rows, ta, T, hist, dev, st); break;
+            case 5: err = bg_hist_d<5>(codes, rows, ta, T, hist, dev, st); break;
+            case 6: err = bg_hist_d<6>(codes, rows, ta, T, hist, dev, st); break;
+            case 7: err = bg_hist_d<7>(codes, rows, ta, T, hist, dev, st); break;
+            case 8: err = bg_hist_d<8>(codes, rows, ta, T, hist, dev, st); break;
+            default: return cudaErrorInvalidValue;
+        }
+        if (err != cudaSuccess) return err;
     }
+    return cudaSuccess;
 }
 
 // vc[row][p] for live leaf row (tree t, leaf q = 4s + j): the leaf pattern p has the

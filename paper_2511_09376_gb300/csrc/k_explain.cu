@@ -1,5 +1,7 @@
 // Depth and tile dispatch of the consumer kernels (k_explain.cuh); the kernels are
 // compiled in the k_explain_d*.cu translation units.
+#include <algorithm>
+
 #include "k_explain.cuh"
 
 namespace wdf {
@@ -13,65 +15,84 @@ WDF_EXPLAIN_DEPTH(7, extern)
 WDF_EXPLAIN_DEPTH(8, extern)
 
 template <int D>
-static cudaError_t explain_depth(const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi,
+static cudaError_t explain_depth(const unsigned char *codes, int64_t n, const ExplainJob &job, float *phi,
                                  int64_t ldp, int tile_rows, const DevInfo &dev, cudaStream_t st) {
     switch (tile_rows) {
-        case 32: return explain_t<D, 32>(C, n, ldc, job, phi, ldp, dev, st);
-        case 128: return explain_t<D, 128>(C, n, ldc, job, phi, ldp, dev, st);
-        default: return explain_t<D, 64>(C, n, ldc, job, phi, ldp, dev, st);
+        case 32: return explain_t<D, 32>(codes, n, job, phi, ldp, dev, st);
+        case 128: return explain_t<D, 128>(codes, n, job, phi, ldp, dev, st);
+        default: return explain_t<D, 64>(codes, n, job, phi, ldp, dev, st);
     }
 }
 
 template <int D>
 static cudaError_t batch_depth(const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items, int *n_items,
-                               int F_max, int tile_rows, int grid, const DevInfo &dev, cudaStream_t st) {
+                               int F_max, int xb_max, int tile_rows, int grid, const DevInfo &dev, cudaStream_t st) {
     switch (tile_rows) {
-        case 32: return batch_t<D, 32>(jobs, reqs, items, n_items, F_max, grid, dev, st);
-        case 128: return batch_t<D, 128>(jobs, reqs, items, n_items, F_max, grid, dev, st);
-        default: return batch_t<D, 64>(jobs, reqs, items, n_items, F_max, grid, dev, st);
+        case 32: return batch_t<D, 32>(jobs, reqs, items, n_items, F_max, xb_max, grid, dev, st);
+        case 128: return batch_t<D, 128>(jobs, reqs, items, n_items, F_max, xb_max, grid, dev, st);
+        default: return batch_t<D, 64>(jobs, reqs, items, n_items, F_max, xb_max, grid, dev, st);
     }
 }
 
-int default_tile_rows(int D, int F, const DevInfo &dev) {
-    const size_t s64 = explain_smem_bytes(D, F, 64);
+int default_tile_rows(int D, int F, int xb, const DevInfo &dev) {
+    const size_t s64 = explain_smem_bytes(D, F, xb, 64);
     return s64 <= dev.smem_optin / 2 ? 64 : 32;
 }
+
+// Rows per encoded chunk: the decision codes of a chunk live in a stream-ordered
+// scratch allocation (so concurrent calls on other streams never share it).
+constexpr int64_t kExplainChunkRows = 1 << 20;
 
 cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi,
                            int64_t ldp, int tile_rows, const DevInfo &dev, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    if (tile_rows <= 0) tile_rows = default_tile_rows(D, job.F, dev);
-    switch (D) {
-        case 2: return explain_depth<2>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
-        case 3: return explain_depth<3>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
-        case 4: return explain_depth<4>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
-        case 5: return explain_depth<5>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
-        case 6: return explain_depth<6>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
-        case 7: return explain_depth<7>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
-        case 8: return explain_depth<8>(C, n, ldc, job, phi, ldp, tile_rows, dev, st);
-        default: return cudaErrorInvalidValue;
+    if (D < 2 || D > 8) return cudaErrorInvalidValue;
+    const int xb = job.ta.n_cols * job.ta.code_bytes;
+    if (tile_rows <= 0) tile_rows = default_tile_rows(D, job.F, xb, dev);
+    const int64_t chunk = std::min(n, kExplainChunkRows);
+    const int64_t pad = 128;  // every tile size divides it
+    unsigned char *codes = nullptr;
+    cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&codes), (size_t)((chunk + pad - 1) / pad * pad) * xb,
+                                      st);
+    if (err != cudaSuccess) return err;
+    for (int64_t r0 = 0; r0 < n && err == cudaSuccess; r0 += chunk) {
+        const int64_t rows = std::min(chunk, n - r0);
+        err = launch_encode_codes(C + r0 * ldc, rows, ldc, job.ta, (rows + pad - 1) / pad * pad, codes, dev, st);
+        if (err != cudaSuccess) break;
+        float *out = phi + r0 * ldp;
+        switch (D) {
+            case 2: err = explain_depth<2>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            case 3: err = explain_depth<3>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            case 4: err = explain_depth<4>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            case 5: err = explain_depth<5>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            case 6: err = explain_depth<6>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            case 7: err = explain_depth<7>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            default: err = explain_depth<8>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+        }
     }
+    const cudaError_t ferr = cudaFreeAsync(codes, st);
+    return err != cudaSuccess ? err : ferr;
 }
 
 cudaError_t launch_explain_batch(int D, const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items,
-                                 int *n_items, int F_max, int tile_rows, int grid, const DevInfo &dev,
+                                 int *n_items, int F_max, int xb_max, int tile_rows, int grid, const DevInfo &dev,
                                  cudaStream_t st) {
     switch (D) {
-        case 2: return batch_depth<2>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
-        case 3: return batch_depth<3>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
-        case 4: return batch_depth<4>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
-        case 5: return batch_depth<5>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
-        case 6: return batch_depth<6>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
-        case 7: return batch_depth<7>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
-        case 8: return batch_depth<8>(jobs, reqs, items, n_items, F_max, tile_rows, grid, dev, st);
+        case 2: return batch_depth<2>(jobs, reqs, items, n_items, F_max, xb_max, tile_rows, grid, dev, st);
+        case 3: return batch_depth<3>(jobs, reqs, items, n_items, F_max, xb_max, tile_rows, grid, dev, st);
+        case 4: return batch_depth<4>(jobs, reqs, items, n_items, F_max, xb_max, tile_rows, grid, dev, st);
+        case 5: return batch_depth<5>(jobs, reqs, items, n_items, F_max, xb_max, tile_rows, grid, dev, st);
+        case 6: return batch_depth<6>(jobs, reqs, items, n_items, F_max, xb_max, tile_rows, grid, dev, st);
+        case 7: return batch_depth<7>(jobs, reqs, items, n_items, F_max, xb_max, tile_rows, grid, dev, st);
+        case 8: return batch_depth<8>(jobs, reqs, items, n_items, F_max, xb_max, tile_rows, grid, dev, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-size_t explain_smem_bytes(int D, int F, int tile_rows) {
+size_t explain_smem_bytes(int D, int F, int xb, int tile_rows) {
     switch (D * 1000 + tile_rows) {
 #define WDF_SMEM_CASE(d, tc) \
-    case d * 1000 + tc: return ExLayout<d>(F, tc).total;
+    case d * 1000 + tc: return ExLayout<d>(F, xb, tc).total;
         WDF_SMEM_CASE(2, 32) WDF_SMEM_CASE(2, 64) WDF_SMEM_CASE(2, 128)
         WDF_SMEM_CASE(3, 32) WDF_SMEM_CASE(3, 64) WDF_SMEM_CASE(3, 128)
         WDF_SMEM_CASE(4, 32) WDF_SMEM_CASE(4, 64) WDF_SMEM_CASE(4, 128)

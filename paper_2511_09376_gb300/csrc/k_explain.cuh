@@ -10,7 +10,7 @@
 // subtree reads a zero row instead.  The slots of the nodes above the bottom subtrees
 // accumulate in registers (one per node, the node-level form of the NumPy indexing of
 // section "Algorithmic Improvements" item 6); every node's value is then added into
-// phi[feature of the node] in the fixed flush order of flush_order.h, eight at a time:
+// phi[feature of the node] in the fixed flush order of tree_layout.h, eight at a time:
 // a batch that repeats no feature reads its eight phi values before writing any, so
 // the shared-memory round trips overlap; any other batch adds one by one.  Pass-through
 // nodes add into a scratch row.  The order of every floating-point addition into a
@@ -22,7 +22,7 @@
 #include <algorithm>
 #include <cstdlib>
 
-#include "flush_order.h"
+#include "tree_layout.h"
 #include "launch.h"
 #include "wdf_device.cuh"
 
@@ -30,7 +30,7 @@ namespace wdf {
 
 template <int D>
 struct ExplainCfg {
-    static constexpr int TCH = 8;  // trees per shared-memory chunk
+    static constexpr int TCH = D >= 8 ? 4 : 8;  // trees per shared-memory chunk
     // bottom subtrees gathered together: the largest power of two (a divisor of NS) whose
     // slot vectors fit in 128 registers
     static constexpr int gs(int g) { return (g > 1 && g * Shape<D>::SP > 128) ? gs(g / 2) : g; }
@@ -39,17 +39,20 @@ struct ExplainCfg {
     static_assert(GS == Shape<D>::NS || (3 * GS) % 8 == 0, "flush batches must not straddle gather groups");
 };
 
+// Shared memory of one block: code tile (TC rows x xb bytes) | phi tile ((F + 1) x (TC + 1)
+// floats, feature-major, row F a scratch row) | tree metadata | node records | phi
+// offsets of the trees' nodes in flush order.
 template <int D>
 struct ExLayout {
-    size_t x, meta, rn, fo, fl, total;
+    size_t x, p, meta, rec, fl, total;
     static __host__ __device__ size_t up(size_t v) { return (v + 15) & ~(size_t)15; }
-    __host__ __device__ ExLayout(int F, int TC) {
-        x = up((size_t)(F + 1) * (TC + 1) * 4);  // one of x and phi
+    __host__ __device__ ExLayout(int F, int xb, int TC) {
+        x = up((size_t)TC * xb);
+        p = up((size_t)(F + 1) * (TC + 1) * 4);
         meta = up((size_t)ExplainCfg<D>::TCH * sizeof(TreeMeta));
-        rn = up((size_t)ExplainCfg<D>::TCH * Shape<D>::NI * sizeof(int2));
-        fo = up((size_t)ExplainCfg<D>::TCH * Shape<D>::NI * sizeof(int));
+        rec = up((size_t)ExplainCfg<D>::TCH * Shape<D>::NI * sizeof(NodeRec));
         fl = up((size_t)ExplainCfg<D>::TCH * flush_len(D) * sizeof(int));
-        total = 2 * x + meta + rn + fo + fl;
+        total = x + p + meta + rec + fl;
     }
 };
 
@@ -68,6 +71,14 @@ __device__ __forceinline__ void ldg_f8(const float4 *p, float4 &a, float4 &b) {
                  : "l"(p));
 }
 
+// phi[o[q]] += val[q], q < cnt, one after another: the rare batch that repeats a
+// feature.  Kept out of line so the per-tree loop stays small in the instruction cache.
+static __device__ __noinline__ void flush_serial(float *myphi, int4 oa, int4 ob, float4 va, float4 vb, int cnt) {
+    const int o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
+    const float v[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+    for (int q = 0; q < cnt; ++q) myphi[o[q]] += v[q];
+}
+
 // phi[o[q]] += val[q] for the first cnt positions of one flush batch.  fast: the batch
 // repeats no real feature, so all reads may precede all writes.
 __device__ __forceinline__ void flush_batch(float *myphi, const int (&o)[8], const float (&val)[8], int cnt,
@@ -81,9 +92,8 @@ __device__ __forceinline__ void flush_batch(float *myphi, const int (&o)[8], con
         for (int q = 0; q < 8; ++q)
             if (q < cnt) myphi[o[q]] = a[q] + val[q];
     } else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (q < cnt) myphi[o[q]] += val[q];
+        flush_serial(myphi, make_int4(o[0], o[1], o[2], o[3]), make_int4(o[4], o[5], o[6], o[7]),
+                     make_float4(val[0], val[1], val[2], val[3]), make_float4(val[4], val[5], val[6], val[7]), cnt);
     }
 }
 
@@ -93,10 +103,13 @@ __device__ __forceinline__ void load_offsets8(const int *p, int (&o)[8]) {
     o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
 }
 
-// One tile of TC consumer rows starting at row c0 of C (n rows), for one ensemble.
-template <int D, int TC>
+// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble.  ENC:
+// the tile's decision codes are computed here from C; otherwise they are copied from
+// codes, the code blocks of all n rows (padded to a multiple of TC rows).
+template <int D, int TC, bool ENC>
 __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float *__restrict__ C, int64_t n,
-                                             int64_t ldc, float *__restrict__ phi, int64_t ldp, int64_t c0,
+                                             int64_t ldc, const unsigned char *__restrict__ codes,
+                                             float *__restrict__ phi, int64_t ldp, int64_t c0,
                                              unsigned char *smem_raw) {
     using S = Shape<D>;
     using X = ExplainCfg<D>;
@@ -108,43 +121,80 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
     const int F = job.F, T = job.T;
     const TreeArrays &ta = job.ta;
     const float *__restrict__ sfold = job.sfold;
-    const ExLayout<D> L(F, TC);
-    float *sx = reinterpret_cast<float *>(smem_raw);
+    const int ncol = ta.n_cols, cb = ta.code_bytes, xb = ncol * cb;
+    const ExLayout<D> L(F, xb, TC);
+    unsigned char *sx = smem_raw;
     float *sp = reinterpret_cast<float *>(smem_raw + L.x);
-    TreeMeta *smeta = reinterpret_cast<TreeMeta *>(smem_raw + 2 * L.x);
-    int2 *srn = reinterpret_cast<int2 *>(smem_raw + 2 * L.x + L.meta);
-    int *sfo = reinterpret_cast<int *>(smem_raw + 2 * L.x + L.meta + L.rn);
-    int *sfl = reinterpret_cast<int *>(smem_raw + 2 * L.x + L.meta + L.rn + L.fo);
+    TreeMeta *smeta = reinterpret_cast<TreeMeta *>(smem_raw + L.x + L.p);
+    int4 *srec = reinterpret_cast<int4 *>(smem_raw + L.x + L.p + L.meta);
+    int *sfl = reinterpret_cast<int *>(smem_raw + L.x + L.p + L.meta + L.rec);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int r = warp; r < TC; r += TC / 32) {
-        const int64_t row = c0 + r;
-        const float *src = C + row * ldc;
-        for (int f = lane; f < F; f += 32) sx[f * XS + r] = (row < n) ? __ldg(src + f) : 0.0f;
+    if constexpr (!ENC) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(codes + c0 * xb);
+        for (int i = tid; i < TC * xb / 16; i += TC) reinterpret_cast<uint4 *>(sx)[i] = __ldg(src + i);
+    } else {
+        // decision codes of the tile's rows (tree_layout.h), in 32-row code blocks.  Thread
+        // tid encodes elements tid + TC * k (row-major over the tile, so a warp reads
+        // consecutive features of a row), eight binary searches in lockstep so that their
+        // threshold loads overlap.
+        for (int k0 = 0; k0 < ncol; k0 += 8) {
+            float x[8];
+            int pos[8], r[8], c[8];
+            CodeCol col[8];
+    #pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int e = tid + TC * (k0 + j);
+                r[j] = e / ncol;
+                c[j] = e - r[j] * ncol;
+                const bool act = k0 + j < ncol;
+                const int4 cv = act ? __ldg(reinterpret_cast<const int4 *>(ta.cols) + c[j]) : make_int4(0, 0, 0, 0);
+                col[j] = CodeCol{cv.x, cv.y, cv.z, cv.w};
+                x[j] = (act && c0 + r[j] < n) ? __ldg(C + (c0 + r[j]) * ldc + cv.x) : 0.0f;
+                pos[j] = 0;
+            }
+            for (int step = cb == 1 ? 128 : 32768; step > 0; step >>= 1) {
+    #pragma unroll
+                for (int j = 0; j < 8; ++j) {  // branch-free: an out-of-range probe reads the first threshold
+                    const bool in = pos[j] + step <= col[j].count;
+                    const float u = __ldg(ta.col_thr + col[j].first + (in ? pos[j] + step - 1 : 0));
+                    pos[j] += (in && u <= x[j]) ? step : 0;
+                }
+            }
+    #pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (k0 + j >= ncol) break;
+                const int code = x[j] != x[j] ? col[j].count : pos[j];
+                unsigned char *dst = sx + (size_t)(r[j] >> 5) * 32 * xb + ((size_t)c[j] * 32 + (r[j] & 31)) * cb;
+                if (cb == 1)
+                    *dst = (unsigned char)code;
+                else
+                    *reinterpret_cast<uint16_t *>(dst) = (uint16_t)code;
+            }
+        }
     }
     for (int i = tid; i < (F + 1) * XS; i += TC) sp[i] = 0.0f;
-    sx[F * XS + tid] = 0.0f;
     float *myphi = sp + tid;
+    const CodeReader xr(sx + (size_t)warp * 32 * xb, lane, cb);
     const float4 *z4 = reinterpret_cast<const float4 *>(job.zero);
     for (int tc0 = 0; tc0 < T; tc0 += X::TCH) {
         const int tcn = min(X::TCH, T - tc0);
         __syncthreads();
-        stage_trees<D>(tc0, tcn, XS, ta.nodes, ta.rn_key, ta.rn_thr, ta.rn_count, ta.pt_mask, ta.live, ta.flush_ok,
-                       srn, sfo, smeta, tid, TC);
-        __syncthreads();
-        // phi offsets of every tree in flush order (padding writes the scratch row)
+        stage_trees<D>(tc0, tcn, ta.rec, ta.meta, srec, smeta, tid, TC);
+        // phi offsets of every tree in flush order (padding and pass-through nodes: the
+        // scratch row F)
         for (int i = tid; i < tcn * FL; i += TC) {
             const int g = i / FL, v = flush_node(D, i - g * FL);
-            sfl[i] = v >= 0 ? sfo[g * S::NI + v] : F * XS;
+            sfl[i] = (v >= 0 ? __ldg(&ta.nodes[(size_t)(tc0 + g) * S::NI + v].x) : F) * XS;
         }
         __syncthreads();
         for (int g = 0; g < tcn; ++g) {
             const int t = tc0 + g;
             const TreeMeta &mt = smeta[g];
             const int *fl = sfl + g * FL;
-            uint64_t dm[S::NW];
-            tree_decisions<D>(srn + g * S::NI, mt, sx, tid, dm);
+            uint32_t dw[S::NW];
+            tree_decisions<D>(srec + g * S::NI, mt, xr, dw);
             uint32_t ent[S::NS];
-            subtree_entries<D>(dm, ent);
+            subtree_entries<D>(dw, ent);
             const uint64_t lv = mt.live;
             const uint32_t fok = mt.flush;
             const float4 *tf = reinterpret_cast<const float4 *>(sfold + (size_t)t * S::NS * S::E * S::SP);
@@ -213,10 +263,10 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
 // 1 block per SM is enough (shared memory limits residency anyway): the register
 // budget then covers a whole gather group in flight.
 template <int D, int TC>
-__global__ void __launch_bounds__(TC, 1) k_explain(const float *__restrict__ C, int64_t n, int64_t ldc,
+__global__ void __launch_bounds__(TC, 1) k_explain(const unsigned char *__restrict__ codes, int64_t n,
                                                    ExplainJob job, float *__restrict__ phi, int64_t ldp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    explain_tile<D, TC>(job, C, n, ldc, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
+    explain_tile<D, TC, false>(job, nullptr, n, 0, codes, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
 }
 
 // Persistent form over a ragged batch: work item i is (job, request, first row).  Blocks
@@ -241,29 +291,29 @@ __global__ void __launch_bounds__(TC, 1) k_explain_batch(const ExplainJob *__res
         const ExplainJob job = jobs[it.x];
         const BatchRequest rq = reqs[it.y];
         const int64_t c0 = ((int64_t)it.z << 31) | (uint32_t)it.w;
-        explain_tile<D, TC>(job, rq.C, rq.n, rq.ldc, rq.phi, rq.ldp, c0, smem_raw);
+        explain_tile<D, TC, true>(job, rq.C, rq.n, rq.ldc, nullptr, rq.phi, rq.ldp, c0, smem_raw);
         __syncthreads();
     }
 }
 
 template <int D, int TC>
-cudaError_t explain_t(const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi, int64_t ldp,
+cudaError_t explain_t(const unsigned char *codes, int64_t n, const ExplainJob &job, float *phi, int64_t ldp,
                       const DevInfo &dev, cudaStream_t st) {
-    const size_t smem = ExLayout<D>(job.F, TC).total;
+    const size_t smem = ExLayout<D>(job.F, job.ta.n_cols * job.ta.code_bytes, TC).total;
     if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
     auto kern = k_explain<D, TC>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     const int64_t blocks = (n + TC - 1) / TC;
-    kern<<<(unsigned)blocks, TC, smem, st>>>(C, n, ldc, job, phi, ldp);
+    kern<<<(unsigned)blocks, TC, smem, st>>>(codes, n, job, phi, ldp);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int D, int TC>
 cudaError_t batch_t(const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items, int *n_items, int F_max,
-                    int grid, const DevInfo &dev, cudaStream_t st) {
-    const size_t smem = ExLayout<D>(F_max, TC).total;
+                    int xb_max, int grid, const DevInfo &dev, cudaStream_t st) {
+    const size_t smem = ExLayout<D>(F_max, xb_max, TC).total;
     if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
     auto kern = k_explain_batch<D, TC>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -282,10 +332,10 @@ cudaError_t batch_t(const ExplainJob *jobs, const BatchRequest *reqs, const int4
 // Explicit instantiation of the kernels of one (depth, tile rows) pair; each pair is
 // compiled in one of the k_explain_d*.cu translation units.
 #define WDF_EXPLAIN_TILE(d, tc, spec)                                                                            \
-    spec template cudaError_t explain_t<d, tc>(const float *, int64_t, int64_t, const ExplainJob &, float *,      \
+    spec template cudaError_t explain_t<d, tc>(const unsigned char *, int64_t, const ExplainJob &, float *,       \
                                                int64_t, const DevInfo &, cudaStream_t);                          \
     spec template cudaError_t batch_t<d, tc>(const ExplainJob *, const BatchRequest *, const int4 *, int *, int,  \
-                                             int, const DevInfo &, cudaStream_t);
+                                             int, int, const DevInfo &, cudaStream_t);
 #define WDF_EXPLAIN_DEPTH(d, spec) WDF_EXPLAIN_TILE(d, 32, spec) WDF_EXPLAIN_TILE(d, 64, spec) \
     WDF_EXPLAIN_TILE(d, 128, spec)
 

@@ -4,20 +4,22 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "tree_layout.h"
+
 namespace wdf {
 
 // Counts kernel launches (every launcher adds the kernels it enqueued).
 void count_launches(int k);
 
-// Device arrays describing the complete layout of an ensemble (see wdf_internal.h).
+// Device arrays describing the complete layout of an ensemble (see wdf_internal.h and
+// tree_layout.h).
 struct TreeArrays {
     const int2 *nodes;        // [T][NI] (feature, threshold bits); feature F = pass-through
-    const int32_t *rn_key;    // [T][NI] compacted real inner nodes: heap | feature << 8
-    const float *rn_thr;      // [T][NI]
-    const int32_t *rn_count;  // [T]
-    const uint64_t *pt_mask;  // [T][4]
-    const uint64_t *live;     // [T]
-    const uint32_t *flush_ok; // [T] bit b: consumer flush batch b repeats no feature
+    const NodeRec *rec;       // [T][NI] real inner nodes of every tree
+    const TreeMeta *meta;     // [T]
+    const CodeCol *cols;      // [n_cols] decision-code columns
+    const float *col_thr;     // their sorted thresholds
+    int n_cols, code_bytes;   // code_bytes: 1 or 2
 };
 
 // Everything the consumer kernel needs about one ensemble.
@@ -41,9 +43,19 @@ struct DevInfo {
 };
 
 // Step 1 of Algorithm 3 (background): joint entry counts hist[T][NS][2^(D+1)] (u32,
-// must be zeroed by the caller) of the background rows at every bottom subtree.
-cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, int F, const TreeArrays &ta, int T,
-                           uint32_t *hist, const DevInfo &dev, cudaStream_t st);
+// must be zeroed by the caller) of the background rows at every bottom subtree.  The
+// rows are encoded to decision codes (tree_layout.h) in chunks of code_rows rows into
+// codes (code_rows * n_cols * code_bytes bytes; code_rows a positive multiple of
+// kBgMaxTileRows), each chunk then counted.
+constexpr int kBgMaxTileRows = 512;
+
+// Decision codes of rows [0, rows) of X (row stride ldx) into codes, in 32-row code
+// blocks (wdf_device.cuh); rows up to rows_pad (a multiple of 32) get code 0.
+cudaError_t launch_encode_codes(const float *X, int64_t rows, int64_t ldx, const TreeArrays &ta, int64_t rows_pad,
+                                unsigned char *codes, const DevInfo &dev, cudaStream_t st);
+cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, const TreeArrays &ta, int T,
+                           unsigned char *codes, int64_t code_rows, uint32_t *hist, const DevInfo &dev,
+                           cudaStream_t st);
 
 // Per-leaf pattern counts vc[row][p] (u32, 2^D per row) of the live leaves, marginals of
 // the joint entry counts; A (nullable) receives them as FP32.
@@ -89,14 +101,16 @@ cudaError_t launch_base_value(int D, const uint32_t *vc, const double *ratio, co
 // 0 picks the default for the shared-memory budget).
 cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi,
                            int64_t ldp, int tile_rows, const DevInfo &dev, cudaStream_t st);
-int default_tile_rows(int D, int F, const DevInfo &dev);
-size_t explain_smem_bytes(int D, int F, int tile_rows);
+// xb: decision-code bytes per row (code columns x code bytes).
+int default_tile_rows(int D, int F, int xb, const DevInfo &dev);
+size_t explain_smem_bytes(int D, int F, int xb, int tile_rows);
 
 // Step 4 for a ragged batch of one depth: a persistent grid (grid <= 0: one wave at full
 // occupancy) walks the work items (job, request, first row split as hi/lo words);
-// *n_items is read on the device.  F_max bounds the feature count of every job.
+// *n_items is read on the device.  F_max and xb_max bound the feature count and the
+// decision-code bytes per row of every job.
 cudaError_t launch_explain_batch(int D, const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items,
-                                 int *n_items, int F_max, int tile_rows, int grid, const DevInfo &dev,
+                                 int *n_items, int F_max, int xb_max, int tile_rows, int grid, const DevInfo &dev,
                                  cudaStream_t st);
 
 // FP64 column means of |phi| and phi: partial sums per row block, then a fixed-order

@@ -10,7 +10,7 @@
 #include <cstring>
 #include <map>
 
-#include "flush_order.h"
+#include "tree_layout.h"
 #include "wdf_internal.h"
 
 namespace wdf {
@@ -60,6 +60,84 @@ void place(const Src &s, int t, int32_t node, int h, int depth, float w, bool ke
     p->node_thr[k] = 1.0f;   // 0 < 1: left
     place(s, t, -1, 2 * h + 1, depth + 1, wl, kl, p, cl);
     place(s, t, -1, 2 * h + 2, depth + 1, 0.0f, false, p, -1);
+}
+
+// Code columns, node records and tree metadata of the decision kernels (tree_layout.h).
+void build_records(Packed *pp) {
+    Packed &p = *pp;
+    const int F = p.F, T = p.T, D = p.D, NI = p.NI;
+    // distinct thresholds of every feature, sorted (NaN thresholds send every row right
+    // and take no part in the codes)
+    std::vector<std::vector<float>> thr(F);
+    for (size_t k = 0; k < p.node_feat.size(); ++k) {
+        const int f = p.node_feat[k];
+        if (f < F && p.node_thr[k] == p.node_thr[k]) thr[(size_t)f].push_back(p.node_thr[k]);
+    }
+    int64_t cols8 = 0, cols16 = 0;
+    for (auto &v : thr) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end(), [](float a, float b) { return a == b; }), v.end());
+        cols8 += ((int64_t)v.size() + 254) / 255;
+        cols16 += ((int64_t)v.size() + 65534) / 65535;
+    }
+    // one-byte codes unless they would take more shared memory than two-byte codes
+    p.code_bytes = cols8 <= 2 * cols16 ? 1 : 2;
+    const int cap = p.code_bytes == 1 ? 255 : 65535;
+    std::vector<int32_t> first_col((size_t)F, -1);
+    p.cols.clear();
+    p.col_thr.clear();
+    for (int f = 0; f < F; ++f) {
+        const auto &v = thr[(size_t)f];
+        if (v.empty()) continue;
+        first_col[(size_t)f] = (int32_t)p.cols.size();
+        for (size_t lo = 0; lo < v.size(); lo += (size_t)cap) {
+            const int cnt = (int)std::min(v.size() - lo, (size_t)cap);
+            int top = 1;
+            while (2 * top <= cnt) top *= 2;
+            p.cols.push_back(CodeCol{f, (int32_t)p.col_thr.size(), cnt, top});
+            p.col_thr.insert(p.col_thr.end(), v.begin() + (int64_t)lo, v.begin() + (int64_t)lo + cnt);
+        }
+    }
+    if (p.cols.empty()) p.cols.push_back(CodeCol{0, 0, 0, 0});  // no real threshold at all
+    const int64_t blk = 32 * (int64_t)p.code_bytes;             // bytes of one column in a code block
+    p.rec.assign((size_t)T * NI, NodeRec{0, -1, 0u, 0u});
+    p.meta.assign((size_t)T, TreeMeta{});
+    for (int t = 0; t < T; ++t) {
+        TreeMeta &m = p.meta[(size_t)t];
+        int c = 0;
+        for (int v = 0; v < NI; ++v) {  // heap order, so the nodes of word v/32 are contiguous
+            const size_t k = (size_t)t * NI + v;
+            const int f = p.node_feat[k];
+            if (f == F) {
+                m.pt[v >> 5] |= 1u << (v & 31);
+            } else {
+                NodeRec r{0, -1, (D >= 7 || v < 32) ? 1u << (v & 31) : 0u, (D <= 6 && v >= 32) ? 1u << (v - 32) : 0u};
+                const float x = p.node_thr[k];
+                if (x == x) {
+                    const auto &u = thr[(size_t)f];
+                    const int64_t j = std::lower_bound(u.begin(), u.end(), x) - u.begin();
+                    r.col_off = (int32_t)((first_col[(size_t)f] + j / cap) * blk);
+                    r.rank = (int32_t)(j % cap);
+                }
+                p.rec[(size_t)t * NI + c++] = r;
+            }
+            if ((v & 31) == 31 || v == NI - 1) m.wend[v >> 5] = (uint8_t)c;
+        }
+        for (int w = (NI - 1) / 32 + 1; w < 8; ++w) m.wend[w] = (uint8_t)c;
+        m.live = p.live[(size_t)t];
+        // flush batches of the consumer kernel whose real features are all distinct
+        for (int b = 0; b < flush_batches(D); ++b) {
+            bool ok = true;
+            for (int i = 8 * b; i < 8 * b + 8 && ok; ++i)
+                for (int j = 8 * b; j < i && ok; ++j) {
+                    const int vi = flush_node(D, i), vj = flush_node(D, j);
+                    if (vi < 0 || vj < 0) continue;
+                    const int32_t fi = p.node_feat[(size_t)t * NI + vi], fj = p.node_feat[(size_t)t * NI + vj];
+                    ok = fi == F || fi != fj;  // pass-through nodes all write the scratch row
+                }
+            if (ok) m.flush |= 1u << b;
+        }
+    }
 }
 
 }  // namespace
@@ -142,42 +220,6 @@ int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const f
     Src s{F, off, feat, thr, left, right, val};
     for (int t = 0; t < T; ++t) place(s, t, 0, 0, 0, 0.0f, false, &p, -1);
 
-    // compact lists of the inner nodes that test a real feature
-    p.rn_count.assign((size_t)T, 0);
-    p.rn_key.assign((size_t)T * p.NI, 0);
-    p.rn_thr.assign((size_t)T * p.NI, 0.0f);
-    p.pt_mask.assign((size_t)T * 4, 0);
-    for (int t = 0; t < T; ++t) {
-        int c = 0;
-        for (int v = 0; v < p.NI; ++v) {
-            const size_t k = (size_t)t * p.NI + v;
-            if (p.node_feat[k] == F) {
-                p.pt_mask[(size_t)t * 4 + (v >> 6)] |= (uint64_t)1 << (v & 63);
-            } else {
-                p.rn_key[(size_t)t * p.NI + c] = v | (p.node_feat[k] << 8);
-                p.rn_thr[(size_t)t * p.NI + c] = p.node_thr[k];
-                ++c;
-            }
-        }
-        p.rn_count[(size_t)t] = c;
-    }
-
-    // flush batches of the consumer kernel whose real features are all distinct
-    p.flush_ok.assign((size_t)T, 0u);
-    for (int t = 0; t < T; ++t) {
-        for (int b = 0; b < flush_batches(p.D); ++b) {
-            bool ok = true;
-            for (int i = 8 * b; i < 8 * b + 8 && ok; ++i)
-                for (int j = 8 * b; j < i && ok; ++j) {
-                    const int vi = flush_node(p.D, i), vj = flush_node(p.D, j);
-                    if (vi < 0 || vj < 0) continue;
-                    const int32_t fi = p.node_feat[(size_t)t * p.NI + vi], fj = p.node_feat[(size_t)t * p.NI + vj];
-                    ok = fi == F || fi != fj;  // pass-through nodes all write the scratch row
-                }
-            if (ok) p.flush_ok[(size_t)t] |= 1u << b;
-        }
-    }
-
     // live bottom subtrees and signature groups of the live leaves
     std::map<uint32_t, std::vector<int32_t>> groups;
     const int D = p.D;
@@ -208,6 +250,7 @@ int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const f
         }
         p.group_off.push_back((int32_t)p.group_leaf.size());
     }
+    build_records(&p);
     return 0;
 }
 

@@ -1,16 +1,23 @@
 // Device helpers shared by the background-count kernel and the consumer kernel.
 //
 // A thread owns one row.  For one tree it evaluates the inner nodes of the complete
-// layout (Def. "decision_tree": x[feature] < threshold), keeps the decisions as a
-// bitmask, and derives the decision patterns of the bottom-subtree roots by the rule
-// of Algorithm 1 (a child's pattern is its parent's shifted left plus 1 when the row
-// takes that child).  Pass-through nodes always send a row left, so their decision
-// bits come from a per-tree mask and only the nodes testing a real feature are
-// evaluated, from a compacted per-tree list.  The pattern indices are compile-time
-// constants of the depth D, so the per-node state stays in registers.
+// layout (Def. "decision_tree": x[feature] < threshold, here on the row's decision
+// codes, tree_layout.h), keeps the decisions as a bitmask, and derives the decision
+// patterns of the bottom-subtree roots by the rule of Algorithm 1 (a child's pattern is
+// its parent's shifted left plus 1 when the row takes that child).  Pass-through nodes
+// always send a row left, so their decision bits come from a per-tree mask and only
+// the nodes testing a real feature are evaluated, from a compacted per-tree list.  The
+// pattern indices are compile-time constants of the depth D, so the per-node state
+// stays in registers.
+//
+// Code tile layout in shared memory (both kernels): blocks of 32 rows; within a block
+// column c occupies 32 consecutive codes, one per row ([block][column][row of block]),
+// so the 32 lanes of a warp read 32 consecutive codes of one column.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "tree_layout.h"
 
 namespace wdf {
 
@@ -20,107 +27,129 @@ struct Shape {
     static constexpr int NL = 1 << D;          // leaves
     static constexpr int NS = 1 << (D - 2);    // bottom subtrees
     static constexpr int E = 1 << (D + 1);     // entries per bottom subtree
-    static constexpr int NW = (NI + 63) / 64;  // 64-bit decision words
+    static constexpr int NW = (NI + 31) / 32;  // 32-bit decision words
     static constexpr int SP = (D + 1) <= 4 ? 4 : ((D + 1) <= 8 ? 8 : 12);  // padded slots per entry
 };
 
-// One tree of a chunk staged in shared memory.
-//   rn[i]  (i < cnt): x = (feature * XS) << 8 | heap index, y = threshold bits
-//   fo[v]  feature * XS of heap node v (pass-through nodes: F * XS, a scratch row)
-struct TreeMeta {
-    uint64_t pt[4];  // pass-through bits
-    uint64_t live;   // live bottom subtrees
-    int cnt;         // real inner nodes
-    uint32_t flush;  // bit b: consumer flush batch b repeats no real feature
+// Stage the node records and metadata of trees [t0, t0 + tcn) into shared memory (all
+// threads of the block call it).
+template <int D>
+__device__ __forceinline__ void stage_trees(int t0, int tcn, const NodeRec *__restrict__ rec,
+                                            const TreeMeta *__restrict__ meta, int4 *srec, TreeMeta *smeta, int tid,
+                                            int nthreads) {
+    constexpr int NI = Shape<D>::NI;
+    const int4 *src = reinterpret_cast<const int4 *>(rec) + (size_t)t0 * NI;
+    for (int i = tid; i < tcn * NI; i += nthreads) srec[i] = __ldg(src + i);
+    const uint2 *msrc = reinterpret_cast<const uint2 *>(meta + t0);
+    uint2 *mdst = reinterpret_cast<uint2 *>(smeta);
+    constexpr int MW = sizeof(TreeMeta) / sizeof(uint2);
+    for (int i = tid; i < tcn * MW; i += nthreads) mdst[i] = __ldg(msrc + i);
+}
+
+// Where a thread reads its row's codes: the 4-byte word holding the row's code in
+// column 0 of its code block, and the byte selector (__byte_perm) that extracts the
+// code from that word, zero-extended, for one- or two-byte codes.
+struct CodeReader {
+    const unsigned char *word;
+    uint32_t sel;
+    __device__ __forceinline__ CodeReader(const unsigned char *block, int lane, int code_bytes) {
+        const int at = lane * code_bytes;
+        word = block + (at & ~3);
+        const uint32_t b = (uint32_t)(at & 3);
+        sel = code_bytes == 1 ? (0x4440u | b) : (0x4400u | ((b + 1u) << 4) | b);
+    }
+    __device__ __forceinline__ int code(int col_off) const {
+        return (int)__byte_perm(*reinterpret_cast<const uint32_t *>(word + col_off), 0u, sel);
+    }
+    // rec.z when the node (rec.x = column offset, rec.y = rank) sends the row left, else
+    // 0; a select, not a branch (the lanes of a warp decide differently)
+    __device__ __forceinline__ uint32_t left_bit(const int4 &rec) const {
+        return (uint32_t)rec.z & (0u - (uint32_t)(code(rec.x) <= rec.y));
+    }
 };
 
-// Stage trees [t0, t0 + tcn) into shared memory (all threads of the block call it).
+// Decision words of one row for one tree: bit v of word v/32 is 1 when the row goes
+// left at inner node v.
 template <int D>
-__device__ __forceinline__ void stage_trees(int t0, int tcn, int XS, const int2 *__restrict__ nodes,
-                                            const int32_t *__restrict__ rn_key, const float *__restrict__ rn_thr,
-                                            const int32_t *__restrict__ rn_count, const uint64_t *__restrict__ pt_mask,
-                                            const uint64_t *__restrict__ live, const uint32_t *__restrict__ flush_ok,
-                                            int2 *srn, int *sfo, TreeMeta *smeta, int tid, int nthreads) {
-    constexpr int NI = Shape<D>::NI;
-    for (int i = tid; i < tcn * NI; i += nthreads) {
-        const size_t gi = (size_t)t0 * NI + i;
-        const int key = __ldg(rn_key + gi);
-        srn[i] = make_int2((((key >> 8) * XS) << 8) | (key & 255), __float_as_int(__ldg(rn_thr + gi)));
-        if (sfo != nullptr) sfo[i] = __ldg(&nodes[gi].x) * XS;
-    }
-    for (int i = tid; i < tcn; i += nthreads) {
-        TreeMeta m;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) m.pt[w] = __ldg(pt_mask + (size_t)(t0 + i) * 4 + w);
-        m.live = __ldg(live + t0 + i);
-        m.cnt = __ldg(rn_count + t0 + i);
-        m.flush = flush_ok != nullptr ? __ldg(flush_ok + t0 + i) : 0u;
-        smeta[i] = m;
-    }
-}
-
-// Decision bitmask of row `lane` (staged at sx[f * XS + lane]) for one tree.
-template <int D>
-__device__ __forceinline__ void tree_decisions(const int2 *rn, const TreeMeta &m, const float *sx, int lane,
-                                               uint64_t (&dm)[Shape<D>::NW]) {
+__device__ __forceinline__ void tree_decisions(const int4 *rec, const TreeMeta &m, const CodeReader &xr,
+                                               uint32_t (&dw)[Shape<D>::NW]) {
     constexpr int NW = Shape<D>::NW;
-    // four independent partial masks, so consecutive nodes do not wait on each other
-    uint64_t part[4][NW];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int w = 0; w < NW; ++w) part[k][w] = 0ull;
-    const int cnt = m.cnt;
-    int i = 0;
-    for (; i + 4 <= cnt; i += 4) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int2 nd = rn[i + k];
-            const float x = sx[(nd.x >> 8) + lane];
-            const uint64_t b = (x < __int_as_float(nd.y)) ? 1ull : 0ull;
-            const int h = nd.x & 255;
-            if (NW == 1) {
-                part[k][0] |= b << h;
-            } else {
-#pragma unroll
-                for (int w = 0; w < NW; ++w) part[k][w] |= ((h >> 6) == w) ? (b << (h & 63)) : 0ull;
+    if constexpr (NW <= 2) {
+        // one loop over all nodes, the bit in a low and a high word (measured much faster
+        // than a loop per word, which stalled on instruction fetch)
+        const int cnt = m.wend[NW - 1];
+        uint32_t l0 = 0u, l1 = 0u, l2 = 0u, l3 = 0u, h0 = 0u, h1 = 0u, h2 = 0u, h3 = 0u;
+        int i = 0;
+        for (; i + 4 <= cnt; i += 4) {
+            const int4 a = rec[i], b = rec[i + 1], c = rec[i + 2], d = rec[i + 3];
+            const uint32_t sa = 0u - (uint32_t)(xr.code(a.x) <= a.y), sb = 0u - (uint32_t)(xr.code(b.x) <= b.y);
+            const uint32_t sc = 0u - (uint32_t)(xr.code(c.x) <= c.y), sd = 0u - (uint32_t)(xr.code(d.x) <= d.y);
+            l0 |= a.z & sa; h0 |= a.w & sa;
+            l1 |= b.z & sb; h1 |= b.w & sb;
+            l2 |= c.z & sc; h2 |= c.w & sc;
+            l3 |= d.z & sd; h3 |= d.w & sd;
+        }
+        for (; i < cnt; ++i) {
+            const int4 a = rec[i];
+            const uint32_t sa = 0u - (uint32_t)(xr.code(a.x) <= a.y);
+            l0 |= a.z & sa; h0 |= a.w & sa;
+        }
+        dw[0] = m.pt[0] | l0 | l1 | l2 | l3;
+        if constexpr (NW == 2) dw[1] = m.pt[1] | h0 | h1 | h2 | h3;
+    } else {
+        // deep trees: one (rolled) loop per 32-node word
+        int lo = 0;
+#pragma unroll 1
+        for (int w = 0; w < NW; ++w) {
+            const int hi = m.wend[w];
+            uint32_t p0 = 0u, p1 = 0u, p2 = 0u, p3 = 0u;
+            int i = lo;
+            for (; i + 4 <= hi; i += 4) {
+                const int4 a = rec[i], b = rec[i + 1], c = rec[i + 2], d = rec[i + 3];
+                p0 |= xr.left_bit(a);
+                p1 |= xr.left_bit(b);
+                p2 |= xr.left_bit(c);
+                p3 |= xr.left_bit(d);
             }
+            for (; i < hi; ++i) p0 |= xr.left_bit(rec[i]);
+            dw[w] = m.pt[w] | p0 | p1 | p2 | p3;
+            lo = hi;
         }
     }
-    for (; i < cnt; ++i) {
-        const int2 nd = rn[i];
-        const float x = sx[(nd.x >> 8) + lane];
-        const uint64_t b = (x < __int_as_float(nd.y)) ? 1ull : 0ull;
-        const int h = nd.x & 255;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) part[0][w] |= ((h >> 6) == w) ? (b << (h & 63)) : 0ull;
-    }
-#pragma unroll
-    for (int w = 0; w < NW; ++w) dm[w] = m.pt[w] | part[0][w] | part[1][w] | part[2][w] | part[3][w];
 }
 
 template <int D>
-__device__ __forceinline__ uint32_t dbit(const uint64_t (&dm)[Shape<D>::NW], int v) {
-    return (uint32_t)(dm[v >> 6] >> (v & 63)) & 1u;
+__device__ __forceinline__ uint32_t dbit(const uint32_t (&dw)[Shape<D>::NW], int v) {
+    return (dw[v >> 5] >> (v & 31)) & 1u;
 }
 
 // Entry index of the row at every bottom subtree (see wdf_internal.h).
 template <int D>
-__device__ __forceinline__ void subtree_entries(const uint64_t (&dm)[Shape<D>::NW], uint32_t (&ent)[Shape<D>::NS]) {
+__device__ __forceinline__ void subtree_entries(const uint32_t (&dw)[Shape<D>::NW], uint32_t (&ent)[Shape<D>::NS]) {
     constexpr int NS = Shape<D>::NS;
     uint32_t pat[2 * NS - 1];
     pat[0] = 0u;
 #pragma unroll
     for (int v = 0; v < NS - 1; ++v) {
-        const uint32_t d = dbit<D>(dm, v);
+        const uint32_t d = dbit<D>(dw, v);
         pat[2 * v + 1] = (pat[v] << 1) | d;
         pat[2 * v + 2] = (pat[v] << 1) | (d ^ 1u);
     }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const int r = NS - 1 + s;
-        ent[s] = (pat[r] << 3) | (dbit<D>(dm, r) << 2) | (dbit<D>(dm, 2 * r + 1) << 1) | dbit<D>(dm, 2 * r + 2);
+        ent[s] = (pat[r] << 3) | (dbit<D>(dw, r) << 2) | (dbit<D>(dw, 2 * r + 1) << 1) | dbit<D>(dw, 2 * r + 2);
     }
+}
+
+// Decision code of value x in one code column (tree_layout.h): the number of the
+// column's sorted thresholds u with u <= x, by binary search; the count for NaN.
+__device__ __forceinline__ int decision_code(float x, const float *__restrict__ u, const CodeCol &c) {
+    if (x != x) return c.count;
+    int pos = 0;
+    for (int step = c.top; step > 0; step >>= 1)
+        if (pos + step <= c.count && __ldg(u + pos + step - 1) <= x) pos += step;
+    return pos;
 }
 
 }  // namespace wdf

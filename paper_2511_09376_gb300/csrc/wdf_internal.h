@@ -21,6 +21,8 @@
 #include <string>
 #include <vector>
 
+#include "tree_layout.h"
+
 namespace wdf {
 
 constexpr int kMaxDepth = 8;
@@ -33,13 +35,14 @@ struct Packed {
     std::vector<float> node_thr;      // [T][NI]
     std::vector<float> leaf_w;        // [T][NL]
     std::vector<uint64_t> live;       // [T] bit s: bottom subtree s has a non-zero leaf
-    // per tree, the inner nodes that test a real feature, compacted: (heap | feature << 8,
-    // threshold bits), rn_count of them; the other inner nodes are pass-through nodes
-    std::vector<int32_t> rn_count;    // [T]
-    std::vector<int32_t> rn_key;      // [T][NI]
-    std::vector<float> rn_thr;        // [T][NI]
-    std::vector<uint64_t> pt_mask;    // [T][4] bit v: inner node v is a pass-through node
-    std::vector<uint32_t> flush_ok;   // [T] bit b: flush batch b repeats no real feature
+    // decision records of the kernels (tree_layout.h): per tree the real inner nodes
+    // (rec[t * NI ...], meta[t].wend[7] of them) and the tree's metadata; the code
+    // columns and their sorted thresholds
+    std::vector<NodeRec> rec;         // [T][NI]
+    std::vector<TreeMeta> meta;       // [T]
+    std::vector<CodeCol> cols;        // [n_cols]
+    std::vector<float> col_thr;       // column segments of the sorted distinct thresholds
+    int code_bytes = 1;               // 1 or 2
     // live leaves grouped by path signature (first-occurrence positions)
     std::vector<uint32_t> sig_key;    // [G] 3 bits per path position
     std::vector<int32_t> group_off;   // [G+1]

@@ -22,18 +22,16 @@ struct wdf_ensemble {
     int64_t bytes = 0;
     // ensemble (load time)
     int2 *d_nodes = nullptr;
-    uint64_t *d_live = nullptr;
     uint32_t *d_keys = nullptr;
     int32_t *d_group_leaf = nullptr;
     int32_t *d_leaf_row = nullptr;
     double *d_w_rows = nullptr;
     int4 *d_tiles = nullptr;
     float *d_t32 = nullptr;
-    int32_t *d_rn_key = nullptr;
-    float *d_rn_thr = nullptr;
-    int32_t *d_rn_count = nullptr;
-    uint64_t *d_pt_mask = nullptr;
-    uint32_t *d_flush_ok = nullptr;
+    wdf::NodeRec *d_rec = nullptr;
+    wdf::TreeMeta *d_meta = nullptr;
+    wdf::CodeCol *d_cols = nullptr;
+    float *d_col_thr = nullptr;
     float *d_zero = nullptr;  // 64 zero bytes: the entry a dead bottom subtree reads
     // tensor-core contraction: K-major tables, 128-row tiles, wait-expiry flag
     float *d_t32t = nullptr;
@@ -41,7 +39,7 @@ struct wdf_ensemble {
     int n_tiles128 = 0;
     int *d_err = nullptr;
     wdf::TreeArrays arrays() const {
-        return wdf::TreeArrays{d_nodes, d_rn_key, d_rn_thr, d_rn_count, d_pt_mask, d_live, d_flush_ok};
+        return wdf::TreeArrays{d_nodes, d_rec, d_meta, d_cols, d_col_thr, (int)pk.cols.size(), pk.code_bytes};
     }
     wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, d_zero, pk.T, pk.F}; }
     // background state (set_background)
@@ -57,6 +55,9 @@ struct wdf_ensemble {
     float *d_stage_in[2] = {nullptr, nullptr};
     float *d_stage_out[2] = {nullptr, nullptr};
     int64_t stage_rows = 0;
+    // decision codes of background rows (one buffer per staging stream)
+    unsigned char *d_codes[2] = {nullptr, nullptr};
+    int64_t code_rows = 0;
     cudaStream_t ist[2] = {nullptr, nullptr};
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
 };
