@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(RT) k_bg_hist(const unsigned char *__restrict_
         for (int g = 0; g < g_cnt; ++g) {
             const TreeMeta &mt = smeta[g];
             uint32_t dw[S::NW];
-            tree_decisions<D>(srec + (size_t)g * S::NI, mt, xr, dw);
+            tree_decisions<D, false>(srec + (size_t)g * S::NI, mt, xr, dw);
             uint32_t ent[S::NS];
             subtree_entries<D>(dw, ent);
             const uint64_t lv = mt.live;
@@ -168,7 +168,7 @@ cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, const 
     for (int64_t r0 = 0; r0 < m; r0 += code_rows) {
         const int64_t rows = std::min(code_rows, m - r0);
         const int64_t rows_pad = (rows + kBgMaxTileRows - 1) / kBgMaxTileRows * kBgMaxTileRows;
-        cudaError_t err = launch_encode_codes(B + r0 * ldb, rows, ldb, ta, rows_pad, codes, dev, st);
+        cudaError_t err = launch_encode_codes(B + r0 * ldb, rows, ldb, ta, rows_pad, codes, st);
         if (err != cudaSuccess) return err;
         switch (D) {
             case 2: err = bg_hist_d<2>(codes, rows, ta, T, hist, dev, st); break;

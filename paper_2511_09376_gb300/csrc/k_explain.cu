@@ -57,7 +57,7 @@ cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const 
     if (err != cudaSuccess) return err;
     for (int64_t r0 = 0; r0 < n && err == cudaSuccess; r0 += chunk) {
         const int64_t rows = std::min(chunk, n - r0);
-        err = launch_encode_codes(C + r0 * ldc, rows, ldc, job.ta, (rows + pad - 1) / pad * pad, codes, dev, st);
+        err = launch_encode_codes(C + r0 * ldc, rows, ldc, job.ta, (rows + pad - 1) / pad * pad, codes, st);
         if (err != cudaSuccess) break;
         float *out = phi + r0 * ldp;
         switch (D) {

@@ -1,13 +1,13 @@
 // Consumer side of Algorithm 3, step 4 (Eq. "bg_shap_derivation" step (g)):
 // phi[c, i] = sum over trees and leaves of s_{l,i}[P[l][c]].
 //
-// One thread per consumer row.  The block stages its rows feature-major in shared
-// memory together with a per-row phi accumulator of the same shape, and the real
-// inner nodes of a chunk of trees.  Per tree the thread evaluates those nodes
-// (decision bitmask in registers), forms its entry at every bottom subtree, and
-// gathers one slot vector per subtree from the folded table -- all gathers of a group
-// of subtrees are issued before any is used, so their L2 latency overlaps; a dead
-// subtree reads a zero row instead.  The slots of the nodes above the bottom subtrees
+// One thread per consumer row.  The block stages its rows' decision codes in shared
+// memory together with a per-row phi accumulator (feature-major), and the real inner
+// nodes of a chunk of trees.  Per tree the thread evaluates those nodes (decision
+// bitmask in registers), forms its entry at every bottom subtree, and gathers one slot
+// vector per subtree from the folded table -- all gathers of a group of subtrees are
+// issued before any is used, so their L2 latency overlaps; a dead subtree reads a zero
+// row instead.  The slots of the nodes above the bottom subtrees
 // accumulate in registers (one per node, the node-level form of the NumPy indexing of
 // section "Algorithmic Improvements" item 6); every node's value is then added into
 // phi[feature of the node] in the fixed flush order of tree_layout.h, eight at a time:
@@ -30,7 +30,9 @@ namespace wdf {
 
 template <int D>
 struct ExplainCfg {
-    static constexpr int TCH = D >= 8 ? 4 : 8;  // trees per shared-memory chunk
+    // trees per shared-memory chunk: two keeps the block small (five blocks of 64 rows
+    // per SM at 127 features), measured faster than eight despite four times the barriers
+    static constexpr int TCH = 2;
     // bottom subtrees gathered together: the largest power of two (a divisor of NS) whose
     // slot vectors fit in 128 registers
     static constexpr int gs(int g) { return (g > 1 && g * Shape<D>::SP > 128) ? gs(g / 2) : g; }
@@ -192,7 +194,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
             const TreeMeta &mt = smeta[g];
             const int *fl = sfl + g * FL;
             uint32_t dw[S::NW];
-            tree_decisions<D>(srec + g * S::NI, mt, xr, dw);
+            tree_decisions<D, false>(srec + g * S::NI, mt, xr, dw);
             uint32_t ent[S::NS];
             subtree_entries<D>(dw, ent);
             const uint64_t lv = mt.live;

@@ -52,7 +52,7 @@ constexpr int kBgMaxTileRows = 512;
 // Decision codes of rows [0, rows) of X (row stride ldx) into codes, in 32-row code
 // blocks (wdf_device.cuh); rows up to rows_pad (a multiple of 32) get code 0.
 cudaError_t launch_encode_codes(const float *X, int64_t rows, int64_t ldx, const TreeArrays &ta, int64_t rows_pad,
-                                unsigned char *codes, const DevInfo &dev, cudaStream_t st);
+                                unsigned char *codes, cudaStream_t st);
 cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, const TreeArrays &ta, int T,
                            unsigned char *codes, int64_t code_rows, uint32_t *hist, const DevInfo &dev,
                            cudaStream_t st);

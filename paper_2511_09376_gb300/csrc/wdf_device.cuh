@@ -68,9 +68,27 @@ struct CodeReader {
     }
 };
 
+template <bool GLOBAL>
+__device__ __forceinline__ int4 load_rec(const int4 *p) {
+    if constexpr (GLOBAL)
+        return __ldg(p);
+    else
+        return *p;
+}
+
+__device__ __forceinline__ TreeMeta load_meta(const TreeMeta *p) {
+    TreeMeta m;
+    const uint2 *src = reinterpret_cast<const uint2 *>(p);
+    uint2 *dst = reinterpret_cast<uint2 *>(&m);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(TreeMeta) / sizeof(uint2)); ++i) dst[i] = __ldg(src + i);
+    return m;
+}
+
 // Decision words of one row for one tree: bit v of word v/32 is 1 when the row goes
-// left at inner node v.
-template <int D>
+// left at inner node v.  GLOBAL: rec points to global memory (read through the
+// read-only cache; every lane reads the same record), else to shared memory.
+template <int D, bool GLOBAL>
 __device__ __forceinline__ void tree_decisions(const int4 *rec, const TreeMeta &m, const CodeReader &xr,
                                                uint32_t (&dw)[Shape<D>::NW]) {
     constexpr int NW = Shape<D>::NW;
@@ -81,7 +99,8 @@ __device__ __forceinline__ void tree_decisions(const int4 *rec, const TreeMeta &
         uint32_t l0 = 0u, l1 = 0u, l2 = 0u, l3 = 0u, h0 = 0u, h1 = 0u, h2 = 0u, h3 = 0u;
         int i = 0;
         for (; i + 4 <= cnt; i += 4) {
-            const int4 a = rec[i], b = rec[i + 1], c = rec[i + 2], d = rec[i + 3];
+            const int4 a = load_rec<GLOBAL>(rec + i), b = load_rec<GLOBAL>(rec + i + 1);
+            const int4 c = load_rec<GLOBAL>(rec + i + 2), d = load_rec<GLOBAL>(rec + i + 3);
             const uint32_t sa = 0u - (uint32_t)(xr.code(a.x) <= a.y), sb = 0u - (uint32_t)(xr.code(b.x) <= b.y);
             const uint32_t sc = 0u - (uint32_t)(xr.code(c.x) <= c.y), sd = 0u - (uint32_t)(xr.code(d.x) <= d.y);
             l0 |= a.z & sa; h0 |= a.w & sa;
@@ -90,7 +109,7 @@ __device__ __forceinline__ void tree_decisions(const int4 *rec, const TreeMeta &
             l3 |= d.z & sd; h3 |= d.w & sd;
         }
         for (; i < cnt; ++i) {
-            const int4 a = rec[i];
+            const int4 a = load_rec<GLOBAL>(rec + i);
             const uint32_t sa = 0u - (uint32_t)(xr.code(a.x) <= a.y);
             l0 |= a.z & sa; h0 |= a.w & sa;
         }
@@ -105,13 +124,14 @@ __device__ __forceinline__ void tree_decisions(const int4 *rec, const TreeMeta &
             uint32_t p0 = 0u, p1 = 0u, p2 = 0u, p3 = 0u;
             int i = lo;
             for (; i + 4 <= hi; i += 4) {
-                const int4 a = rec[i], b = rec[i + 1], c = rec[i + 2], d = rec[i + 3];
+                const int4 a = load_rec<GLOBAL>(rec + i), b = load_rec<GLOBAL>(rec + i + 1);
+                const int4 c = load_rec<GLOBAL>(rec + i + 2), d = load_rec<GLOBAL>(rec + i + 3);
                 p0 |= xr.left_bit(a);
                 p1 |= xr.left_bit(b);
                 p2 |= xr.left_bit(c);
                 p3 |= xr.left_bit(d);
             }
-            for (; i < hi; ++i) p0 |= xr.left_bit(rec[i]);
+            for (; i < hi; ++i) p0 |= xr.left_bit(load_rec<GLOBAL>(rec + i));
             dw[w] = m.pt[w] | p0 | p1 | p2 | p3;
             lo = hi;
         }
