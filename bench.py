@@ -91,6 +91,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# sources whose hash a committed ncu summary must match for its counters to stand
+EXPLAIN_SOURCES = ["k_explain.cuh", "k_explain.cu", "k_codes.cu", "wdf_device.cuh", "tree_layout.h"]
+BACKGROUND_SOURCES = ["k_background.cu", "k_codes.cu", "wdf_device.cuh", "tree_layout.h"]
+
+
 def profiled_traffic(summary: str, sources: list, units: int):
     """DRAM bytes per launch from a committed ncu summary (per-unit figure x units), or
     None when the kernel sources changed since the counters were taken."""
@@ -139,7 +144,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w = synth.WORKLOADS[args.workload]
     t_gen = time.time()
-    ens, C, B = synth.make(w)
+    ens, C, B = synth.make(w, n_consumers=args.consumers, n_background=args.background)
     gen_s = time.time() - t_gen
     n, m, F = C.shape[0], B.shape[0], C.shape[1]
     ctx = wdf.ctx_create(local_rank)
@@ -237,7 +242,9 @@ def run_ours(args, rank, world, local_rank):
             "workload": f"{w.name}: n={n} consumers, m={m} background rows, F={F}, T={w.n_trees} trees, depth<={w.depth}",
             "n_consumers": n, "n_background": m, "n_features": F, "n_trees": w.n_trees, "depth": info["depth"],
             "precision": args.precision, "live_leaves": info["n_live_leaves"], "signatures": info["n_signatures"],
-            "l2": "inputs larger than L2 (B 2.5 GB, C 1.5 GB)", "parallelism": f"replicas{world}",
+            "l2": f"inputs larger than L2 (B {B.nbytes / 1e9:.2f} GB, C {C.nbytes / 1e9:.2f} GB)"
+                  if min(B.nbytes, C.nbytes) > 129e6 else "inputs smaller than L2",
+            "parallelism": f"replicas{world}",
         },
         "explain_ms": explain_ms,
         "background_and_reduce_ms": ms - explain_ms,
@@ -249,7 +256,7 @@ def run_ours(args, rank, world, local_rank):
             "peak": alu_peak_max,
             "unit": "Top/s",
             "frac": achieved / alu_peak_max,
-            "traffic": profiled_traffic("k_explain_large.md", ["k_explain.cu", "wdf_device.cuh"], n),
+            "traffic": profiled_traffic("k_explain_large.md", EXPLAIN_SOURCES, n),
             "algorithmic_bytes": hbm_bytes,
             "ops_per_row": ops,
             "peak_basis": f"{sms} SMs x 128 lanes/clk x {peaks.get('sm_max_mhz', 2070.0)} MHz (max SM clock, {peak_kind})",
@@ -476,6 +483,10 @@ def main():
     ap.add_argument("--workload", default="large")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # smaller cases of the same workload (the same ensemble, the first rows of the same
+    # draws), for profiler captures; the default is the full workload
+    ap.add_argument("--consumers", type=int, default=None, help="consumer rows (default: the workload's)")
+    ap.add_argument("--background", type=int, default=None, help="background rows (default: the workload's)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     ap.add_argument("--duration", type=float, default=30.0, help="serving: seconds of arrivals")
     args = ap.parse_args()
