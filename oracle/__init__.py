@@ -249,3 +249,55 @@ def pd_freq(ens, cover) -> np.ndarray:
     out = np.zeros(hs, dtype=np.float64)
     lib.orc_pd_freq(*_ens_args(ens), _p(_cover(ens, cover)), _p(out))
     return out
+
+
+def wdnf_iv(h, cubes, metric=SHAPLEY) -> np.ndarray:
+    """Interaction values of a WDNF by the per-cube closed forms (h x h, diagonal 0)."""
+    lib = _load()
+    w, off, var, neg = _wdnf_arrays(cubes)
+    out = np.zeros((h, h), dtype=np.float64)
+    rc = lib.orc_wdnf_iv(ctypes.c_int32(h), ctypes.c_int32(len(cubes)), _p(w), _p(off), _p(var), _p(neg),
+                         ctypes.c_int32(metric), _p(out))
+    if rc:
+        raise RuntimeError("orc_wdnf_iv failed")
+    return out
+
+
+def wdnf_iv_bruteforce(h, cubes, metric=SHAPLEY) -> np.ndarray:
+    """Interaction values of a WDNF by the definitions (all assignments of the others)."""
+    lib = _load()
+    w, off, var, neg = _wdnf_arrays(cubes)
+    out = np.zeros((h, h), dtype=np.float64)
+    rc = lib.orc_wdnf_iv_bruteforce(ctypes.c_int32(h), ctypes.c_int32(len(cubes)), _p(w), _p(off), _p(var),
+                                    _p(neg), ctypes.c_int32(metric), _p(out))
+    if rc:
+        raise RuntimeError("orc_wdnf_iv_bruteforce failed")
+    return out
+
+
+def iv_bruteforce(ens, C, B, metric=SHAPLEY) -> np.ndarray:
+    """Interaction values of the background game by the definitions (n x F x F)."""
+    lib = _load()
+    C, n, ldc = _rows(C)
+    B, m, ldb = _rows(B)
+    F = ens.n_features
+    out = np.zeros((n, F, F), dtype=np.float64)
+    rc = lib.orc_iv_bruteforce(*_ens_args(ens), ctypes.c_int32(F), _p(C), ctypes.c_int64(n), ctypes.c_int64(ldc),
+                               _p(B), ctypes.c_int64(m), ctypes.c_int64(ldb), ctypes.c_int32(metric), _p(out))
+    if rc:
+        raise RuntimeError("orc_iv_bruteforce failed")
+    return out
+
+
+def iv_hist(ens, counts, m, C, metric=SHAPLEY) -> np.ndarray:
+    """Interaction values from exact background counts (n x F x F)."""
+    lib = _load()
+    C, n, ld = _rows(C)
+    F = ens.n_features
+    out = np.zeros((n, F, F), dtype=np.float64)
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    rc = lib.orc_iv_hist(*_ens_args(ens), ctypes.c_int32(F), _p(counts), ctypes.c_int64(m),
+                         _p(C), ctypes.c_int64(n), ctypes.c_int64(ld), ctypes.c_int32(metric), _p(out))
+    if rc:
+        raise RuntimeError("orc_iv_hist failed")
+    return out

@@ -26,6 +26,11 @@
  *       background is reduced to exact per-leaf pattern counts vc[l][p_b] computed by
  *       CalcDecisionPatterns (Algorithm 1), then every (consumer pattern, counted
  *       background pattern) cube is valued and weighted by vc/m.
+ * Interaction values (section "Beyond SHAP": Def. "shap_iv_def" for Shapley, Def.
+ * "banzhaf_iv_def" for Banzhaf) of every feature pair of the same background game:
+ *   orc_iv_bruteforce -- v_c(S) for all coalitions, then the definitions written out;
+ *   orc_iv_hist -- the counts of O2 with Table "table_shap_iv" (or Formula
+ *       "banzhaf_simplified_formula_interactions") in place of the value formula.
  * The path-dependent game (covers instead of a background) has the same two ends:
  *   orc_pd_values_bruteforce -- v_c(S) as the cover-weighted expectation walk for all
  *       coalitions, then Eq. "s";
@@ -746,6 +751,204 @@ int orc_pd_values(int32_t n_trees, const int64_t *off, const int32_t *feat, cons
         free(queue);
     }
     free(freq);
+    free_leaves(&ls);
+    return err ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------- interaction values */
+
+/* One satisfiable weighted cube with distinct sets P (a variables) and N (b): for every
+ * ordered pair of its variables i != j, Table "table_shap_iv" (metric 0, cells indexed
+ * by where i and j sit) or Formula "banzhaf_simplified_formula_interactions" (metric
+ * 1, +-w / 2^(|S|-2)), added to out[i * h + j].  Pairs with a variable outside the
+ * cube get 0; the diagonal is not touched. */
+static void cube_iv(const int32_t *P, int a, const int32_t *N, int b, double w, int metric, int32_t h, double *out) {
+    const int s = a + b;
+    if (s < 2) return;
+    double pp, nn, pn, np_;  /* (i in P, j in P), (N, N), (i in P, j in N), (i in N, j in P) */
+    if (metric == ORC_SHAPLEY) {
+        pp = a >= 2 ? w / ((double)(a - 1) * (double)binom(s - 1, a - 1)) : 0.0;
+        nn = b >= 2 ? w / ((double)(b - 1) * (double)binom(s - 1, b - 1)) : 0.0;
+        pn = b >= 1 ? -w / ((double)b * (double)binom(s - 1, b)) : 0.0;
+        np_ = a >= 1 ? -w / ((double)a * (double)binom(s - 1, a)) : 0.0;
+    } else {
+        const double v = w / ldexp(1.0, s - 2);
+        pp = nn = v;
+        pn = np_ = -v;
+    }
+    for (int x = 0; x < a; ++x)
+        for (int y = 0; y < a; ++y)
+            if (x != y) out[(int64_t)P[x] * h + P[y]] += pp;
+    for (int x = 0; x < b; ++x)
+        for (int y = 0; y < b; ++y)
+            if (x != y) out[(int64_t)N[x] * h + N[y]] += nn;
+    for (int x = 0; x < a; ++x)
+        for (int y = 0; y < b; ++y) {
+            out[(int64_t)P[x] * h + N[y]] += pn;
+            out[(int64_t)N[y] * h + P[x]] += np_;
+        }
+}
+
+/* Interaction values of a WDNF by the per-cube closed forms (out is h x h). */
+int orc_wdnf_iv(int32_t h, int32_t K, const double *w, const int64_t *lit_off, const int32_t *lit_var,
+                const uint8_t *lit_neg, int32_t metric, double *out) {
+    for (int64_t i = 0; i < (int64_t)h * h; ++i) out[i] = 0.0;
+    int32_t pos[64], neg[64], P[64], N[64];
+    for (int k = 0; k < K; ++k) {
+        int np = 0, nn = 0, a, b;
+        if (lit_off[k + 1] - lit_off[k] > 64) return -1;
+        for (int64_t j = lit_off[k]; j < lit_off[k + 1]; ++j) {
+            if (lit_neg[j]) neg[nn++] = lit_var[j];
+            else pos[np++] = lit_var[j];
+        }
+        if (!cube_sets(pos, np, neg, nn, P, &a, N, &b)) continue;
+        cube_iv(P, a, N, b, w[k], metric, h, out);
+    }
+    return 0;
+}
+
+/* The pair weight of a coalition of s other players out of h - 2: Def. "shap_iv_def"
+ * is the Shapley value of j in the (h-1)-player game with i held in or out, whose
+ * weight is 1 / ((h-1) C(h-2, s)); Def. "banzhaf_iv_def" takes the uniform average. */
+static double pair_weight(int h, int s, int metric) {
+    return metric == ORC_SHAPLEY ? 1.0 / ((double)(h - 1) * (double)binom(h - 2, s)) : 1.0 / ldexp(1.0, h - 2);
+}
+
+/* Interaction values of a WDNF by the definitions, enumerating the other h-2
+ * variables: sum of weight * (f(i,j) - f(i) - f(j) + f()) over their assignments. */
+int orc_wdnf_iv_bruteforce(int32_t h, int32_t K, const double *w, const int64_t *lit_off, const int32_t *lit_var,
+                           const uint8_t *lit_neg, int32_t metric, double *out) {
+    if (h > 22 || h < 2) return -1;
+    uint8_t x[24];
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < h; ++j) {
+            out[(int64_t)i * h + j] = 0.0;
+            if (i == j) continue;
+            double acc = 0.0;
+            for (uint32_t asg = 0; asg < (1u << (h - 2)); ++asg) {
+                int ones = 0, bit = 0;
+                for (int k = 0; k < h; ++k) {
+                    if (k == i || k == j) continue;
+                    x[k] = (uint8_t)((asg >> bit) & 1u);
+                    ones += x[k];
+                    ++bit;
+                }
+                double f11, f10, f01, f00;
+                x[i] = 1; x[j] = 1; orc_wdnf_eval(h, K, w, lit_off, lit_var, lit_neg, x, &f11);
+                x[i] = 1; x[j] = 0; orc_wdnf_eval(h, K, w, lit_off, lit_var, lit_neg, x, &f10);
+                x[i] = 0; x[j] = 1; orc_wdnf_eval(h, K, w, lit_off, lit_var, lit_neg, x, &f01);
+                x[i] = 0; x[j] = 0; orc_wdnf_eval(h, K, w, lit_off, lit_var, lit_neg, x, &f00);
+                acc += pair_weight(h, ones, metric) * (f11 - f10 - f01 + f00);
+            }
+            out[(int64_t)i * h + j] = acc;
+        }
+    return 0;
+}
+
+/* Def. "shap_iv_def" / "banzhaf_iv_def" on the background game, written out: v_c(S) for
+ * every coalition of the F features, then for every ordered pair i != j the weighted
+ * sum over coalitions S of the other features of v(S+i+j) - v(S+i) - v(S+j) + v(S).
+ * out is n x F x F (diagonal 0).  Tiny F only. */
+int orc_iv_bruteforce(int32_t n_trees, const int64_t *off, const int32_t *feat, const float *thr,
+                      const int32_t *left, const int32_t *right, const float *val, int32_t F,
+                      const float *C, int64_t n, int64_t ldc, const float *B, int64_t m, int64_t ldb,
+                      int32_t metric, double *out) {
+    if (F > 16 || F < 2 || m < 1) return -1;
+    ens_t e = {n_trees, off, feat, thr, left, right, val};
+    const uint32_t NS = 1u << F;
+    int err = 0;
+#pragma omp parallel
+    {
+        double *v = (double *)malloc(sizeof(double) * NS);
+        float *x = (float *)malloc(sizeof(float) * (size_t)F);
+        if (!v || !x) err = 1;
+#pragma omp for schedule(dynamic)
+        for (int64_t c = 0; c < n; ++c) {
+            if (!v || !x) continue;
+            const float *cr = C + c * ldc;
+            for (uint32_t S = 0; S < NS; ++S) {
+                double acc = 0.0;
+                for (int64_t r = 0; r < m; ++r) {
+                    const float *br = B + r * ldb;
+                    for (int i = 0; i < F; ++i) x[i] = ((S >> i) & 1u) ? cr[i] : br[i];
+                    acc += ens_value(&e, x);
+                }
+                v[S] = acc / (double)m;
+            }
+            double *o = out + c * F * F;
+            for (int i = 0; i < F; ++i)
+                for (int j = 0; j < F; ++j) {
+                    double acc = 0.0;
+                    if (i != j) {
+                        const uint32_t bi = 1u << i, bj = 1u << j;
+                        for (uint32_t S = 0; S < NS; ++S) {
+                            if (S & (bi | bj)) continue;
+                            acc += pair_weight(F, __builtin_popcount(S), metric) *
+                                   (v[S | bi | bj] - v[S | bi] - v[S | bj] + v[S]);
+                        }
+                    }
+                    o[i * F + j] = acc;
+                }
+        }
+        free(v);
+        free(x);
+    }
+    return err ? -1 : 0;
+}
+
+/* Interaction values from exact background counts: as orc_values_hist, each (consumer
+ * pattern, counted background pattern) cube weighted by w_l * vc[l][p_b] / m, valued by
+ * Table "table_shap_iv" (or the Banzhaf pair formula).  out is n x F x F. */
+int orc_iv_hist(int32_t n_trees, const int64_t *off, const int32_t *feat, const float *thr,
+                const int32_t *left, const int32_t *right, const float *val, int32_t F,
+                const uint64_t *counts, int64_t m, const float *C, int64_t n, int64_t ldc,
+                int32_t metric, double *out) {
+    if (m < 1) return -1;
+    ens_t e = {n_trees, off, feat, thr, left, right, val};
+    leafset_t ls;
+    if (collect_leaves(&e, &ls)) { free_leaves(&ls); return -1; }
+    int err = 0;
+#pragma omp parallel
+    {
+        uint64_t *pat = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)ls.max_tree_nodes);
+        int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)ls.max_tree_nodes);
+        if (!pat || !queue) err = 1;
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t c = 0; c < n; ++c) {
+            if (!pat || !queue) continue;
+            const float *x = C + c * ldc;
+            double *o = out + c * F * F;
+            for (int64_t i = 0; i < (int64_t)F * F; ++i) o[i] = 0.0;
+            int64_t li = 0;
+            for (int t = 0; t < n_trees; ++t) {
+                row_patterns(&e, t, x, pat, queue);
+                for (; li < ls.n && ls.v[li].tree == t; ++li) {
+                    const leaf_t *L = &ls.v[li];
+                    const int D = L->depth;
+                    const uint64_t full = D == 0 ? 0 : (((uint64_t)1 << D) - 1);
+                    const uint64_t pc = pat[L->node];
+                    int32_t pf[ORC_MAXD];
+                    for (int i = 0; i < D; ++i) pf[i] = feat[off[t] + L->path[i]];
+                    for (uint64_t pb = 0; pb <= full; ++pb) {
+                        uint64_t cnt = counts[L->hoff + (int64_t)pb];
+                        if (cnt == 0) continue;
+                        if ((pc | pb) != full) continue; /* rule 4 */
+                        int32_t pos[ORC_MAXD], neg[ORC_MAXD], P[ORC_MAXD], N[ORC_MAXD];
+                        int np = 0, nn = 0, a, b;
+                        for (int i = 0; i < D; ++i) {
+                            int bc = (int)((pc >> (D - 1 - i)) & 1u), bb = (int)((pb >> (D - 1 - i)) & 1u);
+                            if (bc && !bb) pos[np++] = pf[i];
+                            if (!bc && bb) neg[nn++] = pf[i];
+                        }
+                        if (!cube_sets(pos, np, neg, nn, P, &a, N, &b)) continue;
+                        cube_iv(P, a, N, b, L->w * (double)cnt / (double)m, metric, F, o);
+                    }
+                }
+            }
+        }
+        free(pat);
+        free(queue);
+    }
     free_leaves(&ls);
     return err ? -1 : 0;
 }
