@@ -301,3 +301,29 @@ def iv_hist(ens, counts, m, C, metric=SHAPLEY) -> np.ndarray:
     if rc:
         raise RuntimeError("orc_iv_hist failed")
     return out
+
+
+def pd_iv(ens, cover, C, metric=SHAPLEY) -> np.ndarray:
+    """Path-dependent interaction values, frequency form (n x F x F)."""
+    lib = _load()
+    C, n, ld = _rows(C)
+    F = ens.n_features
+    out = np.zeros((n, F, F), dtype=np.float64)
+    rc = lib.orc_pd_iv(*_ens_args(ens), _p(_cover(ens, cover)), ctypes.c_int32(F), _p(C), ctypes.c_int64(n),
+                       ctypes.c_int64(ld), ctypes.c_int32(metric), _p(out))
+    if rc:
+        raise RuntimeError("orc_pd_iv failed")
+    return out
+
+
+def pd_iv_bruteforce(ens, cover, C, metric=SHAPLEY) -> np.ndarray:
+    """Path-dependent interaction values by the definitions over all coalitions (n x F x F)."""
+    lib = _load()
+    C, n, ld = _rows(C)
+    F = ens.n_features
+    out = np.zeros((n, F, F), dtype=np.float64)
+    rc = lib.orc_pd_iv_bruteforce(*_ens_args(ens), _p(_cover(ens, cover)), ctypes.c_int32(F), _p(C),
+                                  ctypes.c_int64(n), ctypes.c_int64(ld), ctypes.c_int32(metric), _p(out))
+    if rc:
+        raise RuntimeError("orc_pd_iv_bruteforce failed")
+    return out

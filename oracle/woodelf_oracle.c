@@ -896,15 +896,17 @@ int orc_iv_bruteforce(int32_t n_trees, const int64_t *off, const int32_t *feat, 
     return err ? -1 : 0;
 }
 
-/* Interaction values from exact background counts: as orc_values_hist, each (consumer
- * pattern, counted background pattern) cube weighted by w_l * vc[l][p_b] / m, valued by
- * Table "table_shap_iv" (or the Banzhaf pair formula).  out is n x F x F. */
-int orc_iv_hist(int32_t n_trees, const int64_t *off, const int32_t *feat, const float *thr,
-                const int32_t *left, const int32_t *right, const float *val, int32_t F,
-                const uint64_t *counts, int64_t m, const float *C, int64_t n, int64_t ldc,
-                int32_t metric, double *out) {
-    if (m < 1) return -1;
-    ens_t e = {n_trees, off, feat, thr, left, right, val};
+/* Interaction values from per-leaf baseline-pattern weights: as orc_values_hist, each
+ * (consumer pattern, weighted baseline pattern) cube weighted by w_l times the bin's
+ * weight -- vc[l][p_b] / m from exact background counts (counts non-null), or the
+ * path-dependent frequency f_pd[l][p_b] (freq) -- valued by Table "table_shap_iv" (or
+ * the Banzhaf pair formula).  out is n x F x F. */
+static int iv_from_weights(const ens_t *ep, int32_t F, const uint64_t *counts, int64_t m, const double *freq,
+                           const float *C, int64_t n, int64_t ldc, int32_t metric, double *out) {
+    const ens_t e = *ep;
+    const int64_t *off = e.off;
+    const int32_t *feat = e.feat;
+    const int32_t n_trees = e.n_trees;
     leafset_t ls;
     if (collect_leaves(&e, &ls)) { free_leaves(&ls); return -1; }
     int err = 0;
@@ -930,8 +932,9 @@ int orc_iv_hist(int32_t n_trees, const int64_t *off, const int32_t *feat, const 
                     int32_t pf[ORC_MAXD];
                     for (int i = 0; i < D; ++i) pf[i] = feat[off[t] + L->path[i]];
                     for (uint64_t pb = 0; pb <= full; ++pb) {
-                        uint64_t cnt = counts[L->hoff + (int64_t)pb];
-                        if (cnt == 0) continue;
+                        const double wt = counts ? (double)counts[L->hoff + (int64_t)pb] / (double)m
+                                                 : freq[L->hoff + (int64_t)pb];
+                        if (wt == 0.0) continue;
                         if ((pc | pb) != full) continue; /* rule 4 */
                         int32_t pos[ORC_MAXD], neg[ORC_MAXD], P[ORC_MAXD], N[ORC_MAXD];
                         int np = 0, nn = 0, a, b;
@@ -941,7 +944,7 @@ int orc_iv_hist(int32_t n_trees, const int64_t *off, const int32_t *feat, const 
                             if (!bc && bb) neg[nn++] = pf[i];
                         }
                         if (!cube_sets(pos, np, neg, nn, P, &a, N, &b)) continue;
-                        cube_iv(P, a, N, b, L->w * (double)cnt / (double)m, metric, F, o);
+                        cube_iv(P, a, N, b, L->w * wt, metric, F, o);
                     }
                 }
             }
@@ -950,5 +953,73 @@ int orc_iv_hist(int32_t n_trees, const int64_t *off, const int32_t *feat, const 
         free(queue);
     }
     free_leaves(&ls);
+    return err ? -1 : 0;
+}
+
+int orc_iv_hist(int32_t n_trees, const int64_t *off, const int32_t *feat, const float *thr,
+                const int32_t *left, const int32_t *right, const float *val, int32_t F,
+                const uint64_t *counts, int64_t m, const float *C, int64_t n, int64_t ldc,
+                int32_t metric, double *out) {
+    if (m < 1) return -1;
+    ens_t e = {n_trees, off, feat, thr, left, right, val};
+    return iv_from_weights(&e, F, counts, m, NULL, C, n, ldc, metric, out);
+}
+
+/* Path-dependent interaction values: the frequency form (Eq.
+ * "path_dependent_estimation") in place of the counts. */
+int orc_pd_iv(int32_t n_trees, const int64_t *off, const int32_t *feat, const float *thr, const int32_t *left,
+              const int32_t *right, const float *val, const double *cover, int32_t F, const float *C, int64_t n,
+              int64_t ldc, int32_t metric, double *out) {
+    ens_t e = {n_trees, off, feat, thr, left, right, val};
+    leafset_t ls;
+    if (collect_leaves(&e, &ls)) { free_leaves(&ls); return -1; }
+    double *freq = (double *)calloc((size_t)(ls.hist_size > 0 ? ls.hist_size : 1), sizeof(double));
+    if (!freq) { free_leaves(&ls); return -1; }
+    for (int64_t i = 0; i < ls.n; ++i) pd_freq_leaf(&e, cover, &ls.v[i], freq + ls.v[i].hoff);
+    free_leaves(&ls);
+    int rc = iv_from_weights(&e, F, NULL, 0, freq, C, n, ldc, metric, out);
+    free(freq);
+    return rc;
+}
+
+/* Path-dependent interaction values by the definitions: v_c(S) from the cover-weighted
+ * expectation walk for all coalitions, then the pair sums of orc_iv_bruteforce. */
+int orc_pd_iv_bruteforce(int32_t n_trees, const int64_t *off, const int32_t *feat, const float *thr,
+                         const int32_t *left, const int32_t *right, const float *val, const double *cover,
+                         int32_t F, const float *C, int64_t n, int64_t ldc, int32_t metric, double *out) {
+    if (F > 16 || F < 2) return -1;
+    ens_t e = {n_trees, off, feat, thr, left, right, val};
+    const uint32_t NS = 1u << F;
+    int err = 0;
+#pragma omp parallel
+    {
+        double *v = (double *)malloc(sizeof(double) * NS);
+        if (!v) err = 1;
+#pragma omp for schedule(dynamic)
+        for (int64_t c = 0; c < n; ++c) {
+            if (!v) continue;
+            const float *x = C + c * ldc;
+            for (uint32_t S = 0; S < NS; ++S) {
+                double acc = 0.0;
+                for (int t = 0; t < n_trees; ++t) acc += pd_expect(&e, cover, off[t], 0, x, S);
+                v[S] = acc;
+            }
+            double *o = out + c * F * F;
+            for (int i = 0; i < F; ++i)
+                for (int j = 0; j < F; ++j) {
+                    double acc = 0.0;
+                    if (i != j) {
+                        const uint32_t bi = 1u << i, bj = 1u << j;
+                        for (uint32_t S = 0; S < NS; ++S) {
+                            if (S & (bi | bj)) continue;
+                            acc += pair_weight(F, __builtin_popcount(S), metric) *
+                                   (v[S | bi | bj] - v[S | bi] - v[S | bj] + v[S]);
+                        }
+                    }
+                    o[i * F + j] = acc;
+                }
+        }
+        free(v);
+    }
     return err ? -1 : 0;
 }

@@ -71,3 +71,13 @@ def test_stumps_have_no_interactions():
     got = oracle.iv_hist(ens, oracle.bg_hist(ens, B), B.shape[0], C)
     assert np.abs(got).max() < 1e-14
     assert np.abs(oracle.iv_bruteforce(ens, C, B)).max() < 1e-13
+
+
+@pytest.mark.parametrize("metric", METRICS)
+def test_path_dependent_frequency_form_matches_the_definition(metric):
+    ens, C, B = synth.make(synth.Workload("ivpd", 79, 20, 400, 7, 5, 10, 5, 0.5, 0.2, False))
+    cover = synth.node_covers(ens, B)
+    want = oracle.pd_iv_bruteforce(ens, cover, C, metric)
+    got = oracle.pd_iv(ens, cover, C, metric)
+    np.testing.assert_allclose(got, want, atol=1e-12, rtol=1e-12)
+    assert np.abs(want).max() > 0.01
