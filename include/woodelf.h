@@ -140,6 +140,22 @@ wdf_status wdf_set_metric(wdf_ensemble *ens, wdf_metric metric);
 wdf_status wdf_explain(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc, wdf_memkind kind,
                        float *phi, int64_t ldphi, void *stream);
 
+/* Pairwise interaction values of the same game (section "Beyond SHAP"): Shapley
+ * interaction values phi_ij = phi_{j|i=1} - phi_{j|i=0} (Def. "shap_iv_def", computed
+ * per cube with Table "table_shap_iv") when the metric is WDF_SHAPLEY, Banzhaf
+ * interaction values (Def. "banzhaf_iv_def", Formula
+ * "banzhaf_simplified_formula_interactions") when it is WDF_BANZHAF.
+ * C: n x F consumer rows (DEVICE memory, row stride ldc >= F).  out: DEVICE memory, row
+ * r of the result at out + r * ldo (ldo >= F * F), F x F row-major per row: symmetric,
+ * out[i][j] = out[j][i] = the value of the pair (i, j), diagonal 0.  FP32 results from
+ * an FP32 contraction of FP64-built tables; the additions into one element come from
+ * many threads, so the last bits may change between runs.  Stream-ordered; takes a
+ * temporary stream-ordered allocation (pair tables and per-leaf pair vectors).
+ * WDF_EINVAL without a background (or path-dependent frequencies), for null pointers
+ * or short strides. */
+wdf_status wdf_explain_interactions(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc, float *out,
+                                    int64_t ldo, void *stream);
+
 /* E_b f(b), the value of the empty coalition, in FP64 (efficiency property, Appendix
  * B: sum_i phi_i(c) = f(c) - E_b f(b)).  Waits for the background to be processed. */
 wdf_status wdf_expected_value(const wdf_ensemble *ens, double *out, void *stream);

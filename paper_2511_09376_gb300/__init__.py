@@ -25,6 +25,7 @@ from ._binding import (  # noqa: F401
     ensemble_info,
     expected_value,
     explain,
+    explain_interactions,
     global_attribution,
     global_attribution_noalloc,
     launch_count,

@@ -35,6 +35,7 @@ for _name, _args in {
     "wdf_ensemble_info": [_vp, _vp],
     "wdf_set_background": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int, _c.c_int, _vp],
     "wdf_explain": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int, _vp, _c.c_int64, _vp],
+    "wdf_explain_interactions": [_vp, _vp, _c.c_int64, _c.c_int64, _vp, _c.c_int64, _vp],
     "wdf_expected_value": [_vp, _c.POINTER(_c.c_double), _vp],
     "wdf_global_attribution": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int32, _vp, _vp, _vp],
     "wdf_global_attribution_noalloc": [_c.c_int32, _vp, _c.c_int64, _c.c_int64, _c.c_int32, _vp, _vp, _vp],
@@ -208,6 +209,26 @@ def explain(e: Ensemble, C, out=None, stream=None):
         raise ValueError("phi must live in the same memory kind as C and have n rows")
     _check(_lib.wdf_explain(e.handle, _vp(p), int(n), int(ld), kind, _vp(op), int(old), _stream_handle(stream)))
     del keep, okeep
+    return out
+
+
+def explain_interactions(e: Ensemble, C, out=None, stream=None):
+    """Pairwise interaction values (n x F x F float32, symmetric, zero diagonal) of a
+    device tensor of consumer rows, for the ensemble's metric; device tensor out."""
+    p, n, ld, kind, keep = _matrix(C)
+    if kind != MEM_DEVICE:
+        raise ValueError("interaction values take consumer rows in device memory")
+    F = ensemble_info(e)["n_features"]
+    torch = _torch()
+    if out is None:
+        out = torch.empty((n, F, F), dtype=torch.float32, device=C.device)
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float32 and out.dim() == 3
+            and tuple(out.shape) == (n, F, F) and out.stride(2) == 1 and out.stride(1) == F):
+        raise ValueError("out must be a float32 CUDA tensor of shape (n, F, F), rows of F*F contiguous floats")
+    ldo = out.stride(0) if n > 0 else F * F
+    _check(_lib.wdf_explain_interactions(e.handle, _vp(p), int(n), int(ld), _vp(out.data_ptr()), int(ldo),
+                                         _stream_handle(stream)))
+    del keep
     return out
 
 

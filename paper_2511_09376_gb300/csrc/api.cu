@@ -497,6 +497,39 @@ wdf_status wdf_explain(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc
     return WDF_OK;
 }
 
+wdf_status wdf_explain_interactions(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc, float *out,
+                                    int64_t ldo, void *stream) {
+    if (!ens) return fail(WDF_EINVAL, "ens is null");
+    if (!ens->has_bg)
+        return fail(WDF_EINVAL, "wdf_set_background or wdf_set_path_dependent must succeed before interactions");
+    if (n < 0) return fail(WDF_EINVAL, "n < 0");
+    if (n == 0) return WDF_OK;
+    if (!C || !out) return fail(WDF_EINVAL, "C and out must be non-null");
+    const wdf::Packed &p = ens->pk;
+    if (ldc < p.F) return fail(WDF_EINVAL, "ldc < n_features");
+    if (ldo < (int64_t)p.F * p.F) return fail(WDF_EINVAL, "ldo < n_features^2");
+    DeviceGuard g(ens->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int D = p.D, K = 1 << D, P = D * (D - 1) / 2, PP = (P + 3) & ~3;
+    // pair tables, the contraction and its repacking live in one stream-ordered block
+    const size_t n_t2 = (size_t)ens->G * K * P * K, n_s2 = (size_t)ens->n_live * P * K;
+    const size_t n_s2t = (size_t)ens->n_live * K * PP;
+    float *buf = nullptr;
+    WDF_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&buf), std::max<size_t>(n_t2 + n_s2 + n_s2t, 4) * 4, st));
+    float *t2 = buf, *s2 = buf + n_t2, *s2t = buf + n_t2 + n_s2;
+    cudaError_t e = wdf::launch_tables_iv(D, ens->metric, ens->d_keys, ens->G, t2, st);
+    if (e == cudaSuccess)
+        e = wdf::launch_contract_fp32(D, ens->d_A, ens->d_scale, ens->d_tiles, ens->n_tiles, t2, s2, st, P);
+    if (e == cudaSuccess) e = wdf::launch_iv_pack(D, PP, s2, ens->n_live, s2t, st);
+    if (e == cudaSuccess)
+        e = wdf::launch_explain_iv(D, C, n, ldc, p.F, ens->arrays(), p.T, ens->d_group_leaf, ens->n_live, s2t, out,
+                                   ldo, ens->ctx->dev, st);
+    const cudaError_t fe = cudaFreeAsync(buf, st);
+    WDF_CUDA(e);
+    WDF_CUDA(fe);
+    return WDF_OK;
+}
+
 wdf_status wdf_expected_value(const wdf_ensemble *ens, double *out, void *stream) {
     if (!ens || !out) return fail(WDF_EINVAL, "null argument");
     if (!ens->has_bg) return fail(WDF_EINVAL, "no background set");

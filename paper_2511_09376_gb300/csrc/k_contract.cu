@@ -73,7 +73,7 @@ cudaError_t launch_tables(int D, int metric, const uint32_t *sig_keys, int G, fl
 }
 
 // FP32 contraction on CUDA cores: 64 x 64 output tile per block, 4 x 4 per thread.
-__global__ void __launch_bounds__(256) k_contract_fp32(int D, const float *__restrict__ A,
+__global__ void __launch_bounds__(256) k_contract_fp32(int D, int N, const float *__restrict__ A,
                                                        const float *__restrict__ scale, const int4 *__restrict__ tiles,
                                                        const float *__restrict__ t32, float *__restrict__ S) {
     constexpr int BM = 64, BN = 64, BK = 16;
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) k_contract_fp32(int D, const float *__res
     __shared__ float Bs[BK][BN];
     const int4 tile = tiles[blockIdx.x];
     const int g = tile.x, r0 = tile.y, r1 = tile.z;
-    const int K = 1 << D, N = D << D;
+    const int K = 1 << D;
     const int c0 = blockIdx.y * BN;
     if (c0 >= N) return;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -131,11 +131,11 @@ __global__ void __launch_bounds__(256) k_contract_fp32(int D, const float *__res
 }
 
 cudaError_t launch_contract_fp32(int D, const float *A, const float *scale, const int4 *tiles, int n_tiles,
-                                 const float *t32, float *S, cudaStream_t st) {
+                                 const float *t32, float *S, cudaStream_t st, int slots) {
     if (n_tiles == 0) return cudaSuccess;
-    const int N = D << D;
+    const int N = (slots > 0 ? slots : D) << D;
     dim3 grid(n_tiles, (N + 63) / 64);
-    k_contract_fp32<<<grid, 256, 0, st>>>(D, A, scale, tiles, t32, S);
+    k_contract_fp32<<<grid, 256, 0, st>>>(D, N, A, scale, tiles, t32, S);
     count_launches(1);
     return cudaGetLastError();
 }

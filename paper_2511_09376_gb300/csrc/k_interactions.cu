@@ -1,0 +1,277 @@
+// Pairwise interaction values (section "Beyond SHAP": Def. "shap_iv_def" with Table
+// "table_shap_iv", Def. "banzhaf_iv_def" with Formula
+// "banzhaf_simplified_formula_interactions") of the game the ensemble holds.  By
+// linearity (the derivation of Eq. "bg_shap_derivation" uses only linearity) the
+// pipeline is the one of the values with a pair table in place of the value table:
+//   k_tables_iv   per path signature, for every (p_b, p_c) cube and every pair of path
+//                 positions, the pair's cell (FP64 built, stored FP32);
+//   contraction   s2_{l,q}[p_c] = w_l sum_{p_b} M2[p_c][p_b][q] f_l[p_b] (the FP32 GEMM of
+//                 the values with P = D(D-1)/2 pair slots per pattern);
+//   k_iv_pack     s2 per (leaf row, p_c) as PP contiguous floats (P padded to 4);
+//   k_explain_iv  one block per consumer row: the row's decision codes, every tree's
+//                 decision words, then per live leaf its consumer pattern p_c, its PP
+//                 pair values and their features, added (shared-memory atomics) into
+//                 the upper triangle of the row's F x F matrix, written out symmetric
+//                 with a zero diagonal.
+// Unlike the values, the additions into one matrix element come from many threads,
+// so their order (and the last bits of the FP32 result) can change from run to run.
+#include <algorithm>
+
+#include "launch.h"
+#include "wdf_device.cuh"
+
+namespace wdf {
+
+__device__ __forceinline__ double iv_binom(int n, int k) {
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
+    return r;
+}
+
+// One thread per (p_b, p_c) of one signature.  Position pair q runs over (k1, k2), k1 <
+// k2, in the order (0,1), (0,2), ..., (D-2, D-1).  A feature met at several positions
+// is one variable: only pairs of first occurrences carry a value.
+__global__ void k_tables_iv(int D, int metric, const uint32_t *__restrict__ keys, float *__restrict__ t2) {
+    const int g = blockIdx.y;
+    const int K = 1 << D, P = D * (D - 1) / 2, N2 = P << D;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= K * K) return;
+    const int pb = idx >> D, pc = idx & (K - 1);
+    const uint32_t key = keys[g];
+    uint32_t posm = 0, negm = 0;
+    const bool bottom = (pc | pb) != K - 1;  // rule 4
+    for (int k = 0; k < D; ++k) {
+        const int bc = (pc >> (D - 1 - k)) & 1, bb = (pb >> (D - 1 - k)) & 1;
+        const int f = (key >> (3 * k)) & 7;
+        if (bc && !bb) posm |= 1u << f;  // rule 1
+        if (!bc && bb) negm |= 1u << f;  // rule 2
+    }
+    const bool unsat = bottom || (posm & negm);
+    const int a = __popc(posm), b = __popc(negm), s = a + b;
+    double pp = 0.0, nn = 0.0, pn = 0.0, np = 0.0;  // (i in S+, j in S+), (-,-), (+,-), (-,+)
+    if (!unsat && s >= 2) {
+        if (metric == 1) {
+            const double v = 1.0 / (double)(1u << (s - 2));
+            pp = nn = v;
+            pn = np = -v;
+        } else {
+            if (a >= 2) pp = 1.0 / ((double)(a - 1) * iv_binom(s - 1, a - 1));
+            if (b >= 2) nn = 1.0 / ((double)(b - 1) * iv_binom(s - 1, b - 1));
+            if (b >= 1) pn = -1.0 / ((double)b * iv_binom(s - 1, b));
+            if (a >= 1) np = -1.0 / ((double)a * iv_binom(s - 1, a));
+        }
+    }
+    float *row = t2 + ((size_t)g * K + pb) * N2;
+    int q = 0;
+    for (int k1 = 0; k1 < D; ++k1)
+        for (int k2 = k1 + 1; k2 < D; ++k2, ++q) {
+            double v = 0.0;
+            const int f1 = (key >> (3 * k1)) & 7, f2 = (key >> (3 * k2)) & 7;
+            if (!unsat && f1 == k1 && f2 == k2) {
+                const bool p1 = (posm >> k1) & 1u, n1 = (negm >> k1) & 1u;
+                const bool p2 = (posm >> k2) & 1u, n2 = (negm >> k2) & 1u;
+                if (p1 && p2) v = pp;
+                else if (n1 && n2) v = nn;
+                else if (p1 && n2) v = pn;
+                else if (n1 && p2) v = np;
+            }
+            row[((size_t)q << D) + pc] = (float)v;
+        }
+}
+
+cudaError_t launch_tables_iv(int D, int metric, const uint32_t *sig_keys, int G, float *t2, cudaStream_t st) {
+    if (G == 0) return cudaSuccess;
+    const int total = 1 << (2 * D);
+    dim3 grid((total + 255) / 256, G);
+    k_tables_iv<<<grid, 256, 0, st>>>(D, metric, sig_keys, t2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// S2T[row][p_c][0..PP) = S2[row][q * 2^D + p_c] (zeros past P).
+__global__ void k_iv_pack(int D, int PP, const float *__restrict__ S2, int n_live, float *__restrict__ S2T) {
+    const int K = 1 << D, P = D * (D - 1) / 2;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_live * K) return;
+    const int64_t row = idx >> D;
+    const int pc = (int)(idx & (K - 1));
+    const float *src = S2 + (size_t)row * ((size_t)P << D);
+    float *dst = S2T + (size_t)idx * PP;
+    for (int q = 0; q < PP; ++q) dst[q] = q < P ? __ldg(src + ((size_t)q << D) + pc) : 0.0f;
+}
+
+cudaError_t launch_iv_pack(int D, int PP, const float *S2, int n_live, float *S2T, cudaStream_t st) {
+    const int64_t total = (int64_t)n_live << D;
+    if (total == 0) return cudaSuccess;
+    k_iv_pack<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(D, PP, S2, n_live, S2T);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+constexpr int kIvThreads = 256;
+
+// Index of (lo, hi), lo < hi, in the row-major upper triangle of an F x F matrix.
+__device__ __forceinline__ int64_t iv_tri(int lo, int hi, int F) {
+    return (int64_t)lo * F - (int64_t)lo * (lo + 1) / 2 + (hi - lo - 1);
+}
+
+__host__ __device__ __forceinline__ size_t iv_up16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// One block per consumer row (grid-stride over rows).  Shared memory: the row's code
+// per column (int) | every tree's decision words | (SMEM) the upper triangle of the
+// row's matrix.  Without SMEM the triangle accumulates in place in out (global atomics).
+template <int D, bool SMEM>
+__global__ void __launch_bounds__(kIvThreads) k_explain_iv(const float *__restrict__ C, int64_t n, int64_t ldc,
+                                                         int F, TreeArrays ta, int T,
+                                                         const int32_t *__restrict__ group_leaf, int n_live,
+                                                         const float *__restrict__ S2T, float *__restrict__ out,
+                                                         int64_t ldo) {
+    using S = Shape<D>;
+    constexpr int NW = S::NW, NI = S::NI, NL = S::NL, K = 1 << D;
+    constexpr int P = D * (D - 1) / 2, PP = (P + 3) & ~3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ncol = ta.n_cols, cshift = ta.code_bytes == 1 ? 5 : 6;  // column = col_off >> cshift
+    int *scode = reinterpret_cast<int *>(smem_raw);
+    uint32_t *sdw = reinterpret_cast<uint32_t *>(smem_raw + iv_up16((size_t)ncol * 4));
+    float *acc = reinterpret_cast<float *>(smem_raw + iv_up16((size_t)ncol * 4) + iv_up16((size_t)T * NW * 4));
+    const int tid = threadIdx.x;
+    const int64_t ntri = (int64_t)F * (F - 1) / 2;
+    for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
+        float *orow = out + row * ldo;
+        // zero the accumulator; the row's decision codes
+        if (SMEM) {
+            for (int64_t k = tid; k < ntri; k += kIvThreads) acc[k] = 0.0f;
+        } else {
+            for (int64_t k = tid; k < (int64_t)F * F; k += kIvThreads) orow[k] = 0.0f;
+        }
+        const float *x = C + row * ldc;
+        for (int c = tid; c < ncol; c += kIvThreads) {
+            const int4 cv = __ldg(reinterpret_cast<const int4 *>(ta.cols) + c);
+            const CodeCol col{cv.x, cv.y, cv.z, cv.w};
+            scode[c] = decision_code(__ldg(x + col.feature), ta.col_thr + col.first, col);
+        }
+        __syncthreads();
+        // decision words of every tree (bit v of word v / 32: left at inner node v)
+        for (int t = tid; t < T; t += kIvThreads) {
+            const TreeMeta m = load_meta(ta.meta + t);
+            const int4 *rec = reinterpret_cast<const int4 *>(ta.rec) + (size_t)t * NI;
+            if (NW <= 2) {
+                uint32_t lo = 0u, hi = 0u;
+                for (int i = 0; i < m.wend[NW - 1]; ++i) {
+                    const int4 r = __ldg(rec + i);
+                    const uint32_t s = 0u - (uint32_t)(scode[r.x >> cshift] <= r.y);
+                    lo |= (uint32_t)r.z & s;
+                    hi |= (uint32_t)r.w & s;
+                }
+                sdw[t * NW] = m.pt[0] | lo;
+                if (NW == 2) sdw[t * NW + 1] = m.pt[1] | hi;
+            } else {
+                int i = 0;
+                for (int w = 0; w < NW; ++w) {
+                    uint32_t bits = 0u;
+                    for (; i < m.wend[w]; ++i) {
+                        const int4 r = __ldg(rec + i);
+                        bits |= (uint32_t)r.z & (0u - (uint32_t)(scode[r.x >> cshift] <= r.y));
+                    }
+                    sdw[t * NW + w] = m.pt[w] | bits;
+                }
+            }
+        }
+        __syncthreads();
+        // every live leaf: its consumer pattern, its pair values and their features
+        for (int i = tid; i < n_live; i += kIvThreads) {
+            const int id = __ldg(group_leaf + i);
+            const int t = id >> D, q = id & (NL - 1);
+            int pc = 0, fk[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const int h = ((NL + q) >> (D - k)) - 1;  // path node at depth k
+                const uint32_t d = (sdw[t * NW + (h >> 5)] >> (h & 31)) & 1u;
+                pc |= (int)((d ^ ((uint32_t)(q >> (D - 1 - k)) & 1u)) << (D - 1 - k));
+                fk[k] = __ldg(&ta.nodes[(size_t)t * NI + h].x);
+            }
+            float v[PP];
+            const float4 *src = reinterpret_cast<const float4 *>(S2T + ((size_t)i * K + pc) * PP);
+#pragma unroll
+            for (int u = 0; u < PP / 4; ++u) {
+                const float4 w4 = __ldg(src + u);
+                v[4 * u] = w4.x; v[4 * u + 1] = w4.y; v[4 * u + 2] = w4.z; v[4 * u + 3] = w4.w;
+            }
+            int qq = 0;
+#pragma unroll
+            for (int k1 = 0; k1 < D; ++k1)
+#pragma unroll
+                for (int k2 = k1 + 1; k2 < D; ++k2, ++qq) {
+                    const int a = min(fk[k1], fk[k2]), b = max(fk[k1], fk[k2]);
+                    if (v[qq] != 0.0f && b < F && a != b) {
+                        if (SMEM)
+                            atomicAdd(acc + iv_tri(a, b, F), v[qq]);
+                        else
+                            atomicAdd(orow + (size_t)a * F + b, v[qq]);
+                    }
+                }
+        }
+        __syncthreads();
+        // the full symmetric matrix, zero diagonal
+        for (int64_t k = tid; k < (int64_t)F * F; k += kIvThreads) {
+            const int i = (int)(k / F), j = (int)(k - (int64_t)i * F);
+            if (SMEM)
+                orow[k] = i == j ? 0.0f : acc[iv_tri(min(i, j), max(i, j), F)];
+            else if (i > j)
+                orow[k] = orow[(size_t)j * F + i];
+        }
+        __syncthreads();
+    }
+}
+
+size_t iv_smem_bytes(int D, int F, int T, int n_cols, bool smem_acc) {
+    const int NW = ((1 << D) - 1 + 31) / 32;
+    return iv_up16((size_t)n_cols * 4) + iv_up16((size_t)T * NW * 4) +
+           (smem_acc ? iv_up16((size_t)F * (F - 1) / 2 * 4) : 0);
+}
+
+template <int D, bool SMEM>
+static cudaError_t iv_t(const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
+                        const int32_t *group_leaf, int n_live, const float *S2T, float *out, int64_t ldo,
+                        const DevInfo &dev, cudaStream_t st) {
+    const size_t smem = iv_smem_bytes(D, F, T, ta.n_cols, SMEM);
+    if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
+    auto kern = k_explain_iv<D, SMEM>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kIvThreads, smem);
+    if (err != cudaSuccess) return err;
+    const int64_t grid = std::min<int64_t>(n, (int64_t)dev.sms * std::max(per_sm, 1));
+    kern<<<(unsigned)grid, kIvThreads, smem, st>>>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t iv_d(const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
+                        const int32_t *group_leaf, int n_live, const float *S2T, float *out, int64_t ldo,
+                        const DevInfo &dev, cudaStream_t st) {
+    // the triangle in shared memory while two blocks still fit per SM, else in place
+    if (iv_smem_bytes(D, F, T, ta.n_cols, true) <= dev.smem_optin / 2)
+        return iv_t<D, true>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+    return iv_t<D, false>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+}
+
+cudaError_t launch_explain_iv(int D, const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
+                              const int32_t *group_leaf, int n_live, const float *S2T, float *out, int64_t ldo,
+                              const DevInfo &dev, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    switch (D) {
+        case 2: return iv_d<2>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+        case 3: return iv_d<3>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+        case 4: return iv_d<4>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+        case 5: return iv_d<5>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+        case 6: return iv_d<6>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+        case 7: return iv_d<7>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+        case 8: return iv_d<8>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace wdf

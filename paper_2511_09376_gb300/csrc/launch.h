@@ -75,8 +75,9 @@ cudaError_t launch_tables(int D, int metric, const uint32_t *sig_keys, int G, fl
 // Step 3 on CUDA cores: S[row][k * 2^D + p_c] = scale[row] * sum_p A[row][p] *
 // T[g][p][k * 2^D + p_c] for every live leaf row of group g (A: background counts or
 // path-dependent frequencies).  tiles: (group, row0, row_end, 0) items of up to 64 rows.
+// slots: output slots per pattern (0: D, one per path position; D(D-1)/2 for pairs).
 cudaError_t launch_contract_fp32(int D, const float *A, const float *scale, const int4 *tiles, int n_tiles,
-                                 const float *t32, float *S, cudaStream_t st);
+                                 const float *t32, float *S, cudaStream_t st, int slots = 0);
 
 // Step 3 on the tensor cores (tcgen05, TMEM accumulators): the same S as
 // launch_contract_fp32 from split-precision operands, TF32 (bf16 == 0) or BF16 (1).
@@ -112,6 +113,16 @@ size_t explain_smem_bytes(int D, int F, int xb, int tile_rows);
 cudaError_t launch_explain_batch(int D, const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items,
                                  int *n_items, int F_max, int xb_max, int tile_rows, int grid, const DevInfo &dev,
                                  cudaStream_t st);
+
+// Interaction values (k_interactions.cu).  Pair tables t2 [G][2^D][P * 2^D] (P =
+// D(D-1)/2 position pairs) for metric 0 (Shapley) or 1 (Banzhaf); the contraction is
+// launch_contract_fp32 with slots = P; S2T [n_live][2^D][PP] (PP = P rounded up to 4);
+// out [n][F][F] at row stride ldo.
+cudaError_t launch_tables_iv(int D, int metric, const uint32_t *sig_keys, int G, float *t2, cudaStream_t st);
+cudaError_t launch_iv_pack(int D, int PP, const float *S2, int n_live, float *S2T, cudaStream_t st);
+cudaError_t launch_explain_iv(int D, const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
+                              const int32_t *group_leaf, int n_live, const float *S2T, float *out, int64_t ldo,
+                              const DevInfo &dev, cudaStream_t st);
 
 // FP64 column means of |phi| and phi: partial sums per row block, then a fixed-order
 // final sum.  partial holds n_blocks * F * 2 doubles.
