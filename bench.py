@@ -354,6 +354,109 @@ def run_reference(args, world, rank):
     }
 
 
+def interaction_ops(ens) -> dict:
+    """Per consumer row on the real trees: one compare per inner node and one pair
+    lookup-add per (leaf, pair of distinct features on its path)."""
+    compares = adds = 0
+    for t in range(ens.n_trees):
+        o = int(ens.tree_offset[t])
+        stack = [(0, ())]
+        while stack:
+            v, feats = stack.pop()
+            f = int(ens.feature[o + v])
+            if f < 0:
+                k = len(set(feats))
+                adds += k * (k - 1) // 2
+            else:
+                compares += 1
+                stack.append((int(ens.left[o + v]), feats + (f,)))
+                stack.append((int(ens.right[o + v]), feats + (f,)))
+    return {"compares": compares, "pair_adds": adds, "ops": compares + adds}
+
+
+def run_interactions(args):
+    """Shapley interaction values (F x F per consumer) of the large workload's ensemble
+    against a precomputed background: the step is one wdf_explain_interactions call."""
+    import torch
+
+    import oracle
+    import paper_2511_09376_gb300 as wdf
+    from paper_2511_09376_gb300 import synth
+
+    w = synth.WORKLOADS["large"]
+    n = args.consumers or 65536
+    m = args.background or 1_000_000
+    ens, C, B = synth.make(w, n_consumers=n, n_background=m)
+    F = C.shape[1]
+    ctx = wdf.ctx_create(0)
+    e = wdf.load_ensemble(ctx, ens)
+    dB, dC = torch.from_numpy(B).cuda(), torch.from_numpy(C).cuda()
+    wdf.set_background(e, dB)
+    out = torch.empty((n, F, F), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        wdf.explain_interactions(e, dC, out=out)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = wdf.launch_count()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        wdf.explain_interactions(e, dC, out=out)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = wdf.launch_count() - launches0
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    # end to end: host consumer rows in, host interaction matrices out
+    hC = torch.from_numpy(C).pin_memory()
+    hout = torch.empty((n, F, F), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    tt = time.perf_counter()
+    for _ in range(max(1, min(args.steps, 3))):
+        dC.copy_(hC, non_blocking=True)
+        wdf.explain_interactions(e, dC, out=out)
+        hout.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - tt) / max(1, min(args.steps, 3))
+    peaks, peak_kind = _peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    ops = interaction_ops(ens)
+    achieved = ops["ops"] * n / (ms * 1e-3) / 1e12
+    result = {
+        "metric": "background_shapley_interaction_rows_per_sec", "value": n / (ms * 1e-3), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"interactions: large-workload ensemble (T={w.n_trees}, depth<=6, F={F}), n={n} "
+                               f"consumers, background of m={m} rows precomputed (not in the step), "
+                               f"output n x F x F FP32 ({n * F * F * 4 / 1e9:.2f} GB, larger than L2)",
+                   "n_consumers": n, "n_background": m, "n_features": F, "n_trees": w.n_trees},
+        "roofline": {"kernel": "the interaction call: pair tables + contraction + k_iv_pack + k_explain_iv",
+                     "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
+                     "frac": achieved / alu_peak, "traffic": None, "ops_per_row": ops,
+                     "peak_basis": f"{sms} SMs x 128 lanes/clk x {peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind})",
+                     "hbm_gbs": n * F * F * 4 / (ms * 1e-3) / 1e9},
+        "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(C.nbytes),
+                "d2h_bytes_per_step": int(n * F * F * 4)},
+        "gpu_launches": int(launches // args.steps), "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        ns, ms_bg = 8, min(m, 100_000)
+        tb = time.perf_counter()
+        counts = oracle.bg_hist(ens, B[:ms_bg])
+        t_bg = (time.perf_counter() - tb) / ms_bg
+        tc = time.perf_counter()
+        oracle.iv_hist(ens, counts, ms_bg, C[:ns])
+        t_c = (time.perf_counter() - tc) / ns
+        result["cpu_baseline"] = {
+            "value": 1.0 / t_c, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"interaction values of {ns} consumers against counts of {ms_bg} background rows "
+                      f"({t_c * ns:.2f} s; the background counts, {t_bg * ms_bg:.2f} s, are not in the step)"}
+    return result
+
+
 def run_ragged(args):
     """64 ensembles of mixed depth/width: the plain path (one wdf_explain per ensemble, FP32
     contraction) against the batched form (one autotuned graph launch over all of them,
@@ -529,6 +632,9 @@ def main():
         return
     if args.workload == "serving":
         print(json.dumps(run_serving(args)), flush=True)
+        return
+    if args.workload == "interactions":
+        print(json.dumps(run_interactions(args)), flush=True)
         return
     if world > 1:
         import torch
