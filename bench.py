@@ -47,6 +47,11 @@ def max_over_ranks(x: float, world: int, device) -> float:
     return float(t.item())
 
 
+def shard_rows(m: int, rank: int, world: int):
+    """Rows [a, b) of the background that rank counts when the background is sharded."""
+    return m * rank // world, m * (rank + 1) // world
+
+
 def job_rows_per_s(world: int, rows_per_rank: int, seconds: float) -> float:
     """Whole-job throughput: every rank explains its own rows_per_rank rows."""
     return world * rows_per_rank / seconds
@@ -171,10 +176,29 @@ def run_ours(args, rank, world, local_rank):
     phi = torch.empty((n, F), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    shard = None
+    if args.shard_background and world > 1:
+        # every rank counts its slice of the background; one sum of the counts over the
+        # ranks (the only exchange), then each finishes the same background
+        import torch.distributed as dist
+        a, b = shard_rows(m, rank, world)
+        counts = torch.zeros(int(wdf.background_counts_size(e)), dtype=torch.int32, device=dev)
+        shard = (dB[a:b], counts, dist)
+
+    def set_bg():
+        if shard is None:
+            wdf.set_background(e, dB, args.precision)
+            return
+        part, counts, dist = shard
+        counts.zero_()
+        wdf.background_counts(e, part, counts)
+        dist.all_reduce(counts)
+        wdf.set_background_counts(e, counts, m, args.precision)
+
     def step(ev=None):
         if ev is not None:
             ev[2].record(stream)
-        wdf.set_background(e, dB, args.precision)
+        set_bg()
         if ev is not None:
             ev[0].record(stream)
         wdf.explain(e, dC, out=phi)
@@ -257,7 +281,7 @@ def run_ours(args, rank, world, local_rank):
             "precision": args.precision, "live_leaves": info["n_live_leaves"], "signatures": info["n_signatures"],
             "l2": f"inputs larger than L2 (B {B.nbytes / 1e9:.2f} GB, C {C.nbytes / 1e9:.2f} GB)"
                   if min(B.nbytes, C.nbytes) > 129e6 else "inputs smaller than L2",
-            "parallelism": f"replicas{world}",
+            "parallelism": f"background-sharded{world}" if shard is not None else f"replicas{world}",
         },
         "explain_ms": explain_ms,
         "background_ms": background_ms,
@@ -616,6 +640,8 @@ def main():
     # draws), for profiler captures; the default is the full workload
     ap.add_argument("--consumers", type=int, default=None, help="consumer rows (default: the workload's)")
     ap.add_argument("--background", type=int, default=None, help="background rows (default: the workload's)")
+    ap.add_argument("--shard-background", action="store_true",
+                    help="N > 1: each rank counts 1/N of the background rows, the counts are summed over ranks")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     ap.add_argument("--duration", type=float, default=30.0, help="serving: seconds of arrivals")
     args = ap.parse_args()

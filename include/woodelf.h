@@ -108,6 +108,26 @@ wdf_status wdf_ensemble_info(const wdf_ensemble *ens, wdf_info *out);
 wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, wdf_memkind kind,
                               wdf_precision precision, void *stream);
 
+/* The background in shards (for background rows split across devices or arriving in
+ * parts): step 1 of Algorithm 3 produces joint pattern counts that are plain sums over
+ * the background rows (Eq. "bg_shap_derivation" step (d)), so the counts of disjoint
+ * shards add up to the counts of their union.
+ * wdf_background_counts_size: the number of u32 counts (T * 2^(D-2) * 2^(D+1)); -1 for
+ * a null ensemble.
+ * wdf_background_counts: ADDS the counts of rows B (DEVICE memory, m x F, stride ldb)
+ * into counts (DEVICE memory, wdf_background_counts_size u32, zeroed by the caller
+ * before the first shard).  Shares the ensemble's code buffer with wdf_set_background:
+ * calls on one ensemble must not overlap on the GPU.
+ * wdf_set_background_counts: finishes the background from summed counts (DEVICE
+ * memory) of m_total rows in total, exactly as wdf_set_background would from all the
+ * rows at once (the same counts give the same tables, folded vectors and results).
+ * WDF_EUNSUPPORTED for m_total < 1 or more than 2^32 - 1 rows. */
+int64_t wdf_background_counts_size(const wdf_ensemble *ens);
+wdf_status wdf_background_counts(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, uint32_t *counts,
+                                 void *stream);
+wdf_status wdf_set_background_counts(wdf_ensemble *ens, const uint32_t *counts, int64_t m_total,
+                                     wdf_precision precision, void *stream);
+
 /*
  * Path-Dependent values (section "Efficient Path-Dependent SHAP Equation"): the
  * baseline pattern frequencies come from the nodes' covers (the number of training rows

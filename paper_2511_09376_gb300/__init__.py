@@ -11,6 +11,8 @@ from ._binding import (  # noqa: F401
     Batch,
     batch_autotune,
     batch_create,
+    background_counts,
+    background_counts_size,
     batch_explain,
     batch_tile_rows,
     FP32,
@@ -26,6 +28,7 @@ from ._binding import (  # noqa: F401
     expected_value,
     explain,
     explain_interactions,
+    set_background_counts,
     global_attribution,
     global_attribution_noalloc,
     launch_count,

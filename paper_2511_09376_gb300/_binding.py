@@ -36,6 +36,8 @@ for _name, _args in {
     "wdf_set_background": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int, _c.c_int, _vp],
     "wdf_explain": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int, _vp, _c.c_int64, _vp],
     "wdf_explain_interactions": [_vp, _vp, _c.c_int64, _c.c_int64, _vp, _c.c_int64, _vp],
+    "wdf_background_counts": [_vp, _vp, _c.c_int64, _c.c_int64, _vp, _vp],
+    "wdf_set_background_counts": [_vp, _vp, _c.c_int64, _c.c_int, _vp],
     "wdf_expected_value": [_vp, _c.POINTER(_c.c_double), _vp],
     "wdf_global_attribution": [_vp, _vp, _c.c_int64, _c.c_int64, _c.c_int32, _vp, _vp, _vp],
     "wdf_global_attribution_noalloc": [_c.c_int32, _vp, _c.c_int64, _c.c_int64, _c.c_int32, _vp, _vp, _vp],
@@ -49,6 +51,8 @@ for _name, _args in {
 }.items():
     getattr(_lib, _name).argtypes = _args
     getattr(_lib, _name).restype = _c.c_int
+_lib.wdf_background_counts_size.argtypes = [_vp]
+_lib.wdf_background_counts_size.restype = _c.c_int64
 _lib.wdf_launch_count.argtypes = []
 _lib.wdf_launch_count.restype = _c.c_int64
 _lib.wdf_ctx_destroy.argtypes = [_vp]
@@ -189,6 +193,36 @@ def set_background(e: Ensemble, B, precision="fp32", stream=None) -> None:
     prec = _PRECISION[precision] if isinstance(precision, str) else int(precision)
     _check(_lib.wdf_set_background(e.handle, _vp(p), int(m), int(ld), kind, prec, _stream_handle(stream)))
     del keep
+
+
+def background_counts_size(e: Ensemble) -> int:
+    return int(_lib.wdf_background_counts_size(e.handle))
+
+
+def background_counts(e: Ensemble, B, counts=None, stream=None):
+    """Joint pattern counts of the background rows B (a device tensor), ADDED into counts
+    (a device uint32 tensor of background_counts_size elements; zeros when None)."""
+    torch = _torch()
+    p, m, ld, kind, keep = _matrix(B)
+    if kind != MEM_DEVICE:
+        raise ValueError("background shards take rows in device memory")
+    size = int(_lib.wdf_background_counts_size(e.handle))
+    if counts is None:
+        counts = torch.zeros(size, dtype=torch.int32, device=B.device)
+    if not (counts.is_cuda and counts.dtype in (torch.int32, torch.uint32) and counts.numel() == size
+            and counts.is_contiguous()):
+        raise ValueError(f"counts must be a contiguous CUDA int32/uint32 tensor of {size} elements")
+    _check(_lib.wdf_background_counts(e.handle, _vp(p), int(m), int(ld), _vp(counts.data_ptr()),
+                                      _stream_handle(stream)))
+    del keep
+    return counts
+
+
+def set_background_counts(e: Ensemble, counts, m_total: int, precision="fp32", stream=None) -> None:
+    """Finish the background from summed shard counts of m_total rows in total."""
+    prec = _PRECISION[precision] if isinstance(precision, str) else int(precision)
+    _check(_lib.wdf_set_background_counts(e.handle, _vp(counts.data_ptr()), int(m_total), prec,
+                                          _stream_handle(stream)))
 
 
 def explain(e: Ensemble, C, out=None, stream=None):

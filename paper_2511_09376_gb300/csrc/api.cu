@@ -220,6 +220,21 @@ wdf_status contract_and_fold(wdf_ensemble *ens, wdf_precision precision, cudaStr
     return WDF_OK;
 }
 
+// Steps 2-3 of Algorithm 3 after the joint counts are in d_hist: per-leaf counts (and
+// the FP32 frequency operand), scales w_l / m, E_b f(b), contraction and fold.
+wdf_status finish_background(wdf_ensemble *ens, int64_t m, wdf_precision precision, cudaStream_t st) {
+    const wdf::Packed &p = ens->pk;
+    WDF_CUDA(wdf::launch_leaf_counts(p.D, ens->d_hist, ens->d_group_leaf, ens->n_live, ens->d_vc, ens->d_A, st));
+    WDF_CUDA(wdf::launch_scale(ens->d_w_rows, ens->n_live, m, ens->d_scale, st));
+    WDF_CUDA(wdf::launch_base_value(p.D, ens->d_vc, nullptr, ens->d_w_rows, ens->n_live, m, ens->d_base, st));
+    wdf_status s1 = contract_and_fold(ens, precision, st);
+    if (s1 != WDF_OK) return s1;
+    ens->m = m;
+    ens->pd = 0;
+    ens->has_bg = 1;
+    return WDF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -412,16 +427,51 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
             WDF_CUDA(cudaStreamWaitEvent(st, ens->ev_join[i], 0));
         }
     }
-    WDF_CUDA(wdf::launch_leaf_counts(p.D, ens->d_hist, ens->d_group_leaf, ens->n_live, ens->d_vc, ens->d_A, st));
-    WDF_CUDA(wdf::launch_scale(ens->d_w_rows, ens->n_live, m, ens->d_scale, st));
-    WDF_CUDA(wdf::launch_base_value(p.D, ens->d_vc, nullptr, ens->d_w_rows, ens->n_live, m, ens->d_base, st));
-    wdf_status s1 = contract_and_fold(ens, precision, st);
+    wdf_status s1 = finish_background(ens, m, precision, st);
     if (s1 != WDF_OK) return s1;
     if (kind == WDF_MEM_HOST) WDF_CUDA(cudaStreamSynchronize(st));
-    ens->m = m;
-    ens->pd = 0;
-    ens->has_bg = 1;
     return WDF_OK;
+}
+
+int64_t wdf_background_counts_size(const wdf_ensemble *ens) {
+    if (!ens) return -1;
+    const wdf::Packed &p = ens->pk;
+    return (int64_t)p.T * p.NS * (2 << p.D);
+}
+
+wdf_status wdf_background_counts(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, uint32_t *counts,
+                                 void *stream) {
+    if (!ens) return fail(WDF_EINVAL, "ens is null");
+    if (m < 0) return fail(WDF_EINVAL, "m < 0");
+    if (m == 0) return WDF_OK;
+    if (!B || !counts) return fail(WDF_EINVAL, "B and counts must be non-null");
+    if (ldb < ens->pk.F) return fail(WDF_EINVAL, "ldb < n_features");
+    if (m > (int64_t)0xFFFFFFFF) return fail(WDF_EUNSUPPORTED, "more than 2^32-1 background rows");
+    DeviceGuard g(ens->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const wdf::Packed &p = ens->pk;
+    wdf_status s = ensure_codes(ens, m, 1);
+    if (s != WDF_OK) return s;
+    WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, ens->arrays(), p.T, ens->d_codes[0], ens->code_rows, counts,
+                                 ens->ctx->dev, st));
+    return WDF_OK;
+}
+
+wdf_status wdf_set_background_counts(wdf_ensemble *ens, const uint32_t *counts, int64_t m_total,
+                                     wdf_precision precision, void *stream) {
+    if (!ens) return fail(WDF_EINVAL, "ens is null");
+    if (!counts) return fail(WDF_EINVAL, "counts is null");
+    if (m_total < 1) return fail(WDF_EUNSUPPORTED, "empty background (m_total < 1)");
+    if (m_total > (int64_t)0xFFFFFFFF) return fail(WDF_EUNSUPPORTED, "more than 2^32-1 background rows");
+    if (precision != WDF_FP32 && precision != WDF_TF32X3 && precision != WDF_BF16X3)
+        return fail(WDF_EINVAL, "unknown precision");
+    DeviceGuard g(ens->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    wdf_status s0 = ensure_frequency_state(ens, precision);
+    if (s0 != WDF_OK) return s0;
+    WDF_CUDA(cudaMemcpyAsync(ens->d_hist, counts, (size_t)wdf_background_counts_size(ens) * 4,
+                             cudaMemcpyDeviceToDevice, st));
+    return finish_background(ens, m_total, precision, st);
 }
 
 wdf_status wdf_set_covers(wdf_ensemble *ens, const double *cover) {

@@ -58,6 +58,41 @@ def test_two_ranks_take_the_slowest_rank_and_count_all_rows():
         assert rows_per_s == pytest.approx(2 * 1000 / 0.5)
 
 
+def _shard_rank(rank, world, port, out):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2511_09376_gb300 import synth
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        b = _bench()
+        ens, _, B = synth.make("tiny")
+        lo, hi = b.shard_rows(B.shape[0], rank, world)
+        counts = torch.from_numpy(oracle.bg_hist(ens, B[lo:hi]).astype(np.int64))
+        dist.all_reduce(counts)  # the one exchange of the sharded background
+        out.put((rank, lo, hi, bool(np.array_equal(counts.numpy(), oracle.bg_hist(ens, B).astype(np.int64)))))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_background_counts_sum_to_the_whole():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [(lo, hi) for _, lo, hi, _ in got] == [(0, 100), (100, 200)]
+    assert all(ok for *_, ok in got)
+
+
 def test_single_rank_needs_no_process_group():
     b = _bench()
     assert b.max_over_ranks(0.125, 1, None) == 0.125
