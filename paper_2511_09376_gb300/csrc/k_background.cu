@@ -205,13 +205,14 @@ __global__ void k_leaf_counts(int D, const uint32_t *__restrict__ hist, const in
     const uint32_t dn = (j < 2) ? fn : (fn ^ 1u);         // path goes left at r for j < 2
     const uint32_t dch = ((j & 1) == 0) ? fc : (fc ^ 1u);  // and left at the child for even j
     const uint32_t *h = hist + ((size_t)t * NS + s) * E;
+    const uint32_t R = pp ^ (uint32_t)s;  // ancestors' raw decisions (wdf_internal.h)
     uint32_t e0, e1;
-    if (j < 2) {
-        e0 = (pp << 3) | (dn << 2) | (dch << 1) | 0u;
-        e1 = e0 | 1u;
-    } else {
-        e0 = (pp << 3) | (dn << 2) | 0u | dch;
+    if (j < 2) {  // the path takes 2r+1 (entry bit 0); sum over the decision at 2r+2
+        e0 = (R << 3) | (dn << 2) | dch;
         e1 = e0 | 2u;
+    } else {  // the path takes 2r+2 (entry bit 1); sum over the decision at 2r+1
+        e0 = (R << 3) | (dn << 2) | (dch << 1);
+        e1 = e0 | 1u;
     }
     const uint32_t v = __ldg(h + e0) + __ldg(h + e1);
     vc[idx] = v;

@@ -154,7 +154,8 @@ __global__ void k_fold(int D, const float *__restrict__ S, const int32_t *__rest
     const int e = (int)(idx % E);
     const int s = (int)((idx / E) % NS);
     const int t = (int)(idx / ((int64_t)E * NS));
-    const uint32_t pp = (uint32_t)e >> 3, dn = (e >> 2) & 1, dnl = (e >> 1) & 1, dnr = e & 1;
+    // entry -> pattern at the subtree root and the three decisions (wdf_internal.h)
+    const uint32_t pp = ((uint32_t)e >> 3) ^ (uint32_t)s, dn = (e >> 2) & 1, dnl = e & 1, dnr = (e >> 1) & 1;
     float out[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[k] = 0.0f;

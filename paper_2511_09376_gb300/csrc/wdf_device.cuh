@@ -143,22 +143,27 @@ __device__ __forceinline__ uint32_t dbit(const uint32_t (&dw)[Shape<D>::NW], int
     return (dw[v >> 5] >> (v & 31)) & 1u;
 }
 
-// Entry index of the row at every bottom subtree (see wdf_internal.h).
+// Two adjacent decision bits, v and v + 1 (bit 0 = node v), of the decision words.
+template <int D>
+__device__ __forceinline__ uint32_t dbit2(const uint32_t (&dw)[Shape<D>::NW], int v) {
+    if ((v & 31) != 31) return (dw[v >> 5] >> (v & 31)) & 3u;
+    return ((dw[v >> 5] >> 31) | (dw[(v >> 5) + 1] << 1)) & 3u;
+}
+
+// Entry index of the row at every bottom subtree (wdf_internal.h): the ancestors' raw
+// decisions R are built once per node of depth < D-2 (siblings share them), then each
+// entry takes d_r and the adjacent pair d_{2r+1}, d_{2r+2} in one extraction.
 template <int D>
 __device__ __forceinline__ void subtree_entries(const uint32_t (&dw)[Shape<D>::NW], uint32_t (&ent)[Shape<D>::NS]) {
     constexpr int NS = Shape<D>::NS;
-    uint32_t pat[2 * NS - 1];
-    pat[0] = 0u;
+    uint32_t R[NS > 1 ? NS - 1 : 1];  // R of the children of node v, v < NS - 1
 #pragma unroll
-    for (int v = 0; v < NS - 1; ++v) {
-        const uint32_t d = dbit<D>(dw, v);
-        pat[2 * v + 1] = (pat[v] << 1) | d;
-        pat[2 * v + 2] = (pat[v] << 1) | (d ^ 1u);
-    }
+    for (int v = 0; v < NS - 1; ++v) R[v] = ((v == 0 ? 0u : R[(v - 1) >> 1]) << 1) | dbit<D>(dw, v);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const int r = NS - 1 + s;
-        ent[s] = (pat[r] << 3) | (dbit<D>(dw, r) << 2) | (dbit<D>(dw, 2 * r + 1) << 1) | dbit<D>(dw, 2 * r + 2);
+        const uint32_t Rr = r == 0 ? 0u : R[(r - 1) >> 1];
+        ent[s] = (Rr << 3) | (dbit<D>(dw, r) << 2) | dbit2<D>(dw, 2 * r + 1);
     }
 }
 

@@ -14,8 +14,10 @@
 // "Bottom subtree" s (0 <= s < NS = 2^(D-2)) is the complete subtree of height 2 rooted
 // at heap node r = NS - 1 + s: three inner nodes r, 2r+1, 2r+2 and four leaves 4s..4s+3.
 // Everything consumer-side is indexed by the "entry" of a row at a bottom subtree:
-//   e = (pp << 3) | (d_r << 2) | (d_{2r+1} << 1) | d_{2r+2},
-// pp = the row's decision pattern at r (D-2 bits, root first), d_v = split at node v.
+//   e = (R << 3) | (d_r << 2) | (d_{2r+2} << 1) | d_{2r+1},
+// d_v = 1 when the row goes left at node v, R = the d of the D-2 ancestors of r (root
+// first).  The row's decision pattern at r (Algorithm 1: bit = the row follows the
+// path to r) is R ^ s, since s's bits root first are the path's turns (1 = right).
 #pragma once
 #include <cstdint>
 #include <string>
