@@ -82,7 +82,10 @@ __global__ void __launch_bounds__(RT) k_bg_hist(const unsigned char *__restrict_
         for (int g = 0; g < g_cnt; ++g) {
             const TreeMeta &mt = smeta[g];
             uint32_t dw[S::NW];
-            tree_decisions<D, false>(srec + (size_t)g * S::NI, mt, xr, dw);
+            if (cb == 1)
+                tree_decisions<D, true>(srec + (size_t)g * S::NI, mt, xr, dw);
+            else
+                tree_decisions<D, false>(srec + (size_t)g * S::NI, mt, xr, dw);
             uint32_t ent[S::NS];
             subtree_entries<D>(dw, ent);
             const uint64_t lv = mt.live;

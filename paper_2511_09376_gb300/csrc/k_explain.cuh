@@ -194,6 +194,8 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
             const TreeMeta &mt = smeta[g];
             const int *fl = sfl + g * FL;
             uint32_t dw[S::NW];
+            // one generic decision loop for both code widths (a second, one-byte copy in
+            // this loop measured slower here, unlike in the counting kernel)
             tree_decisions<D, false>(srec + g * S::NI, mt, xr, dw);
             uint32_t ent[S::NS];
             subtree_entries<D>(dw, ent);

@@ -46,35 +46,37 @@ __device__ __forceinline__ void stage_trees(int t0, int tcn, const NodeRec *__re
     for (int i = tid; i < tcn * MW; i += nthreads) mdst[i] = __ldg(msrc + i);
 }
 
-// Where a thread reads its row's codes: the 4-byte word holding the row's code in
-// column 0 of its code block, and the byte selector (__byte_perm) that extracts the
-// code from that word, zero-extended, for one- or two-byte codes.
+// Where a thread reads its row's codes: its own code in column 0 of its code block
+// (one-byte codes: a plain byte load), or the 4-byte word holding it and the byte
+// selector (__byte_perm) that extracts the code, zero-extended, for two-byte codes.
 struct CodeReader {
-    const unsigned char *word;
+    const unsigned char *byte, *word;
     uint32_t sel;
     __device__ __forceinline__ CodeReader(const unsigned char *block, int lane, int code_bytes) {
         const int at = lane * code_bytes;
+        byte = block + at;
         word = block + (at & ~3);
         const uint32_t b = (uint32_t)(at & 3);
         sel = code_bytes == 1 ? (0x4440u | b) : (0x4400u | ((b + 1u) << 4) | b);
     }
+    template <bool ONE_BYTE>
     __device__ __forceinline__ int code(int col_off) const {
-        return (int)__byte_perm(*reinterpret_cast<const uint32_t *>(word + col_off), 0u, sel);
+        if constexpr (ONE_BYTE)
+            return (int)byte[col_off];
+        else
+            return (int)__byte_perm(*reinterpret_cast<const uint32_t *>(word + col_off), 0u, sel);
     }
     // rec.z when the node (rec.x = column offset, rec.y = rank) sends the row left, else
     // 0; a select, not a branch (the lanes of a warp decide differently)
+    template <bool ONE_BYTE>
     __device__ __forceinline__ uint32_t left_bit(const int4 &rec) const {
-        return (uint32_t)rec.z & (0u - (uint32_t)(code(rec.x) <= rec.y));
+        return (uint32_t)rec.z & (0u - (uint32_t)(code<ONE_BYTE>(rec.x) <= rec.y));
+    }
+    template <bool ONE_BYTE>
+    __device__ __forceinline__ uint32_t left_mask(const int4 &rec) const {
+        return 0u - (uint32_t)(code<ONE_BYTE>(rec.x) <= rec.y);
     }
 };
-
-template <bool GLOBAL>
-__device__ __forceinline__ int4 load_rec(const int4 *p) {
-    if constexpr (GLOBAL)
-        return __ldg(p);
-    else
-        return *p;
-}
 
 __device__ __forceinline__ TreeMeta load_meta(const TreeMeta *p) {
     TreeMeta m;
@@ -86,9 +88,8 @@ __device__ __forceinline__ TreeMeta load_meta(const TreeMeta *p) {
 }
 
 // Decision words of one row for one tree: bit v of word v/32 is 1 when the row goes
-// left at inner node v.  GLOBAL: rec points to global memory (read through the
-// read-only cache; every lane reads the same record), else to shared memory.
-template <int D, bool GLOBAL>
+// left at inner node v.  rec (shared memory) holds the tree's real inner nodes.
+template <int D, bool ONE_BYTE>
 __device__ __forceinline__ void tree_decisions(const int4 *rec, const TreeMeta &m, const CodeReader &xr,
                                                uint32_t (&dw)[Shape<D>::NW]) {
     constexpr int NW = Shape<D>::NW;
@@ -99,18 +100,17 @@ __device__ __forceinline__ void tree_decisions(const int4 *rec, const TreeMeta &
         uint32_t l0 = 0u, l1 = 0u, l2 = 0u, l3 = 0u, h0 = 0u, h1 = 0u, h2 = 0u, h3 = 0u;
         int i = 0;
         for (; i + 4 <= cnt; i += 4) {
-            const int4 a = load_rec<GLOBAL>(rec + i), b = load_rec<GLOBAL>(rec + i + 1);
-            const int4 c = load_rec<GLOBAL>(rec + i + 2), d = load_rec<GLOBAL>(rec + i + 3);
-            const uint32_t sa = 0u - (uint32_t)(xr.code(a.x) <= a.y), sb = 0u - (uint32_t)(xr.code(b.x) <= b.y);
-            const uint32_t sc = 0u - (uint32_t)(xr.code(c.x) <= c.y), sd = 0u - (uint32_t)(xr.code(d.x) <= d.y);
+            const int4 a = rec[i], b = rec[i + 1], c = rec[i + 2], d = rec[i + 3];
+            const uint32_t sa = xr.left_mask<ONE_BYTE>(a), sb = xr.left_mask<ONE_BYTE>(b);
+            const uint32_t sc = xr.left_mask<ONE_BYTE>(c), sd = xr.left_mask<ONE_BYTE>(d);
             l0 |= a.z & sa; h0 |= a.w & sa;
             l1 |= b.z & sb; h1 |= b.w & sb;
             l2 |= c.z & sc; h2 |= c.w & sc;
             l3 |= d.z & sd; h3 |= d.w & sd;
         }
         for (; i < cnt; ++i) {
-            const int4 a = load_rec<GLOBAL>(rec + i);
-            const uint32_t sa = 0u - (uint32_t)(xr.code(a.x) <= a.y);
+            const int4 a = rec[i];
+            const uint32_t sa = xr.left_mask<ONE_BYTE>(a);
             l0 |= a.z & sa; h0 |= a.w & sa;
         }
         dw[0] = m.pt[0] | l0 | l1 | l2 | l3;
@@ -124,14 +124,12 @@ __device__ __forceinline__ void tree_decisions(const int4 *rec, const TreeMeta &
             uint32_t p0 = 0u, p1 = 0u, p2 = 0u, p3 = 0u;
             int i = lo;
             for (; i + 4 <= hi; i += 4) {
-                const int4 a = load_rec<GLOBAL>(rec + i), b = load_rec<GLOBAL>(rec + i + 1);
-                const int4 c = load_rec<GLOBAL>(rec + i + 2), d = load_rec<GLOBAL>(rec + i + 3);
-                p0 |= xr.left_bit(a);
-                p1 |= xr.left_bit(b);
-                p2 |= xr.left_bit(c);
-                p3 |= xr.left_bit(d);
+                p0 |= xr.left_bit<ONE_BYTE>(rec[i]);
+                p1 |= xr.left_bit<ONE_BYTE>(rec[i + 1]);
+                p2 |= xr.left_bit<ONE_BYTE>(rec[i + 2]);
+                p3 |= xr.left_bit<ONE_BYTE>(rec[i + 3]);
             }
-            for (; i < hi; ++i) p0 |= xr.left_bit(load_rec<GLOBAL>(rec + i));
+            for (; i < hi; ++i) p0 |= xr.left_bit<ONE_BYTE>(rec[i]);
             dw[w] = m.pt[w] | p0 | p1 | p2 | p3;
             lo = hi;
         }
