@@ -38,12 +38,20 @@ __global__ void __launch_bounds__(kEncodeThreads) k_encode_codes(const float *__
         for (int c = warp; c < cn; c += kEncodeThreads / 32) {
             const int4 cv = __ldg(reinterpret_cast<const int4 *>(ta.cols) + c0 + c);
             const CodeCol col{cv.x, cv.y, cv.z, cv.w};
-            const int code =
-                valid ? decision_code(xs[lane * (kEncodeCols + 1) + c], ta.col_thr + col.first, col) : 0;
-            if (cb == 1)
+            const float x = xs[lane * (kEncodeCols + 1) + c];
+            if (cb == 1) {
+                // binary search from the column's top power of two (the same for the whole
+                // warp) over its 255 padded entries: NaN padding is never <= x, so no bound
+                // checks; a NaN x gets the count, as in decision_code
+                const float *u = ta.col_thr + col.first;
+                int pos = 0;
+                for (int step = col.top; step > 0; step >>= 1) pos += __ldg(u + pos + step - 1) <= x ? step : 0;
+                const int code = !valid ? 0 : (x != x ? col.count : pos);
                 dst[(size_t)(c0 + c) * 32 + lane] = (unsigned char)code;
-            else
+            } else {
+                const int code = valid ? decision_code(x, ta.col_thr + col.first, col) : 0;
                 reinterpret_cast<uint16_t *>(dst)[(size_t)(c0 + c) * 32 + lane] = (uint16_t)code;
+            }
         }
     }
 }

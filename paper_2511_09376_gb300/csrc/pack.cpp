@@ -8,6 +8,7 @@
 // pattern-pair table.
 #include <algorithm>
 #include <cstring>
+#include <limits>
 #include <map>
 
 #include "tree_layout.h"
@@ -96,9 +97,16 @@ void build_records(Packed *pp) {
             while (2 * top <= cnt) top *= 2;
             p.cols.push_back(CodeCol{f, (int32_t)p.col_thr.size(), cnt, top});
             p.col_thr.insert(p.col_thr.end(), v.begin() + (int64_t)lo, v.begin() + (int64_t)lo + cnt);
+            // one-byte columns are padded to 255 entries with NaN (u <= x is false for a NaN
+            // u), so the encoder can search them in 8 fixed steps without bound checks
+            if (p.code_bytes == 1)
+                p.col_thr.insert(p.col_thr.end(), (size_t)(255 - cnt), std::numeric_limits<float>::quiet_NaN());
         }
     }
-    if (p.cols.empty()) p.cols.push_back(CodeCol{0, 0, 0, 0});  // no real threshold at all
+    if (p.cols.empty()) {  // no real threshold at all: one empty column
+        p.cols.push_back(CodeCol{0, 0, 0, 0});
+        if (p.code_bytes == 1) p.col_thr.assign(255, std::numeric_limits<float>::quiet_NaN());
+    }
     const int64_t blk = 32 * (int64_t)p.code_bytes;             // bytes of one column in a code block
     p.rec.assign((size_t)T * NI, NodeRec{0, -1, 0u, 0u});
     p.meta.assign((size_t)T, TreeMeta{});

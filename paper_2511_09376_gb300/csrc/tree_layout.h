@@ -49,7 +49,8 @@ static_assert(sizeof(NodeRec) == 16, "NodeRec is one 16-byte load");
 static_assert(sizeof(TreeMeta) == 56, "TreeMeta layout");
 
 // One code column: source feature, first threshold in the sorted threshold array,
-// threshold count, and the largest power of two <= count (0 when count is 0).
+// threshold count, and the largest power of two <= count (0 when count is 0).  With
+// one-byte codes every column occupies 255 entries of the array (NaN after its count).
 struct CodeCol {
     int32_t feature, first, count, top;
 };

@@ -260,6 +260,24 @@ def test_degenerate_trees_nan_ties_and_single_rows(wdf, ctx):
     np.testing.assert_array_equal(one, phi[7:8])
 
 
+def test_constant_trees_and_nan_thresholds(wdf, ctx):
+    # only single-leaf trees (no threshold at all), then a tree whose only split has a
+    # NaN threshold (every row goes right): values zero / only the constant part
+    rng = np.random.default_rng(9)
+    B = rng.standard_normal((50, 3)).astype(np.float32)
+    C = rng.standard_normal((20, 3)).astype(np.float32)
+    const = _tree_ensemble(3, [[(-1, 0, -1, -1, 0.5)], [(-1, 0, -1, -1, -1.25)]])
+    e, phi = _run(wdf, ctx, const, C, B)
+    assert not phi.any()
+    assert wdf.expected_value(e) == pytest.approx(-0.75)
+    nanthr = _tree_ensemble(3, [[(1, float("nan"), 1, 2, 0.0), (-1, 0, -1, -1, 3.0), (-1, 0, -1, -1, -2.0)],
+                                [(0, 0.0, 1, 2, 0.0), (-1, 0, -1, -1, 1.0), (-1, 0, -1, -1, 0.5)]])
+    e, phi = _run(wdf, ctx, nanthr, C, B)
+    want = oracle.values_hist(nanthr, oracle.bg_hist(nanthr, B), B.shape[0], C)
+    assert_phi_close(phi, want)
+    assert not phi[:, 1].any() and not phi[:, 2].any()
+
+
 def test_empty_and_error_paths(wdf, ctx):
     import torch
     ens, C, B = synth.make("tiny")
