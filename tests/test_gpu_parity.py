@@ -172,7 +172,9 @@ def test_phi_large_sampled_rows(wdf, ctx):
     del dB
     dC = _dev(C)
     phi = wdf.explain(e, dC)
-    rows = np.unique(np.concatenate([np.linspace(0, C.shape[0] - 1, 48).astype(np.int64), [0, 63, 64, C.shape[0] - 1]]))
+    seams = [(1 << 20) - 1, 1 << 20, (1 << 21) - 1, 1 << 21]  # the encoded 2^20-row chunks of one call
+    rows = np.unique(np.concatenate([np.linspace(0, C.shape[0] - 1, 48).astype(np.int64),
+                                     [0, 63, 64, C.shape[0] - 1], seams]))
     got = phi[torch.from_numpy(rows).to(phi.device)].cpu().numpy()
     counts = oracle.bg_hist(ens, B)
     want = oracle.values_hist(ens, counts, B.shape[0], C[rows])
