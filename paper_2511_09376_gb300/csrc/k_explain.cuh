@@ -228,12 +228,16 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
 #pragma unroll
                     for (int k = 0; k < D - 2; ++k) acc[((r + 1) >> (D - 2 - k)) - 1] += vj[k];
                 }
-                // the three inner nodes of each subtree of the group, in flush order
+                // the three inner nodes of each subtree of the group, in flush order; the
+                // next batch's phi offsets are read before this batch's phi writes, so the
+                // offset loads stay off the chain of dependent shared-memory round trips
+                int o[8];
+                load_offsets8(fl + 3 * s0, o);
 #pragma unroll
                 for (int i0 = 0; i0 < 3 * GS; i0 += 8) {
                     const int fb = 3 * s0 + i0;
-                    int o[8];
-                    load_offsets8(fl + fb, o);
+                    int on[8];
+                    if (i0 + 8 < 3 * GS) load_offsets8(fl + fb + 8, on);
                     float val[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
@@ -241,17 +245,29 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
                         val[q] = i < 3 * GS ? reinterpret_cast<const float *>(&v[i / 3][0])[D - 2 + i % 3] : 0.0f;
                     }
                     flush_batch(myphi, o, val, min(8, 3 * GS - i0), (fok >> (fb >> 3)) & 1u);
+                    if (i0 + 8 < 3 * GS) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) o[q] = on[q];
+                    }
                 }
             }
             // the nodes above the bottom subtrees
-#pragma unroll
-            for (int u0 = 0; u0 < S::NS - 1; u0 += 8) {
+            if (S::NS > 1) {
                 int o[8];
-                load_offsets8(fl + FLB + u0, o);
-                float val[8];
+                load_offsets8(fl + FLB, o);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) val[q] = u0 + q < S::NS - 1 ? acc[u0 + q] : 0.0f;
-                flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u);
+                for (int u0 = 0; u0 < S::NS - 1; u0 += 8) {
+                    int on[8];
+                    if (u0 + 8 < S::NS - 1) load_offsets8(fl + FLB + u0 + 8, on);
+                    float val[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) val[q] = u0 + q < S::NS - 1 ? acc[u0 + q] : 0.0f;
+                    flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u);
+                    if (u0 + 8 < S::NS - 1) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) o[q] = on[q];
+                    }
+                }
             }
         }
     }
