@@ -98,7 +98,9 @@ wdf_status wdf_ensemble_info(const wdf_ensemble *ens, wdf_info *out);
 /*
  * Set the background B (m x F, leading dimension ldb) and run the consumer-independent
  * half of Algorithm 3: background pattern counts (step 1), pattern-pair tables (step
- * 2) and their contraction (step 3), in the given precision.  B is not retained.
+ * 2) and their contraction (step 3), in the given precision.  B is not retained; its
+ * decision codes pass through a buffer the ensemble keeps (up to 2^20 rows of codes).
+ * Calls on one ensemble must not overlap on the GPU.
  * WDF_EUNSUPPORTED: m == 0 (an empty background is the path-dependent variant).
  * precision WDF_TF32X3 / WDF_BF16X3 runs the contraction on the tensor cores (tcgen05,
  * TMEM accumulators) and then waits for the stream to check the kernel's bounded waits:
@@ -154,8 +156,12 @@ wdf_status wdf_set_metric(wdf_ensemble *ens, wdf_metric metric);
  * phi[c, i] for the n consumer rows C (leading dimension ldc) into phi (leading
  * dimension ldphi >= F): Algorithm 3 step 4 / Eq. "bg_shap_derivation" step (g).
  * C and phi live in the same memory kind.  WDF_EINVAL if no background was set.
- * Device kind: asynchronous.  Host kind: copies through device staging buffers and
- * returns once phi is written on the host.
+ * Device kind: asynchronous; the rows' decision codes (one or two bytes per code column
+ * and row, at most 2^20 rows at a time) live in a temporary stream-ordered allocation,
+ * so calls on different streams never share scratch memory.  Host kind: copies
+ * through the ensemble's device staging buffers and returns once phi is written on the
+ * host.  phi of a row does not depend on the other rows of the call (the same
+ * floating-point additions in the same order).
  */
 wdf_status wdf_explain(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc, wdf_memkind kind,
                        float *phi, int64_t ldphi, void *stream);
