@@ -562,18 +562,22 @@ wdf_status wdf_explain_interactions(wdf_ensemble *ens, const float *C, int64_t n
     cudaStream_t st = (cudaStream_t)stream;
     const int D = p.D, K = 1 << D, P = D * (D - 1) / 2, PP = (P + 3) & ~3;
     // pair tables, the contraction and its repacking live in one stream-ordered block
+    // depth <= 6: pair values folded per bottom-subtree entry; deeper: per leaf
+    const bool folded = D <= 6;
     const size_t n_t2 = (size_t)ens->G * K * P * K, n_s2 = (size_t)ens->n_live * P * K;
-    const size_t n_s2t = (size_t)ens->n_live * K * PP;
+    const size_t n_s2t = folded ? wdf::iv_fold_floats(D, p.T) : (size_t)ens->n_live * K * PP;
     float *buf = nullptr;
     WDF_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&buf), std::max<size_t>(n_t2 + n_s2 + n_s2t, 4) * 4, st));
     float *t2 = buf, *s2 = buf + n_t2, *s2t = buf + n_t2 + n_s2;
     cudaError_t e = wdf::launch_tables_iv(D, ens->metric, ens->d_keys, ens->G, t2, st);
     if (e == cudaSuccess)
         e = wdf::launch_contract_fp32(D, ens->d_A, ens->d_scale, ens->d_tiles, ens->n_tiles, t2, s2, st, P);
-    if (e == cudaSuccess) e = wdf::launch_iv_pack(D, PP, s2, ens->n_live, s2t, st);
     if (e == cudaSuccess)
-        e = wdf::launch_explain_iv(D, C, n, ldc, p.F, ens->arrays(), p.T, ens->d_group_leaf, ens->n_live, s2t, out,
-                                   ldo, ens->ctx->dev, st);
+        e = folded ? wdf::launch_iv_fold(D, s2, ens->d_leaf_row, p.T, s2t, st)
+                   : wdf::launch_iv_pack(D, PP, s2, ens->n_live, s2t, st);
+    if (e == cudaSuccess)
+        e = wdf::launch_explain_iv(D, C, n, ldc, p.F, ens->arrays(), p.T, ens->d_group_leaf, ens->n_live,
+                                   folded ? nullptr : s2t, folded ? s2t : nullptr, out, ldo, ens->ctx->dev, st);
     const cudaError_t fe = cudaFreeAsync(buf, st);
     WDF_CUDA(e);
     WDF_CUDA(fe);

@@ -7,12 +7,15 @@
 //                 positions, the pair's cell (FP64 built, stored FP32);
 //   contraction   s2_{l,q}[p_c] = w_l sum_{p_b} M2[p_c][p_b][q] f_l[p_b] (the FP32 GEMM of
 //                 the values with P = D(D-1)/2 pair slots per pattern);
-//   k_iv_pack     s2 per (leaf row, p_c) as PP contiguous floats (P padded to 4);
-//   k_explain_iv  one block per consumer row: the row's decision codes, every tree's
-//                 decision words, then per live leaf its consumer pattern p_c, its PP
-//                 pair values and their features, added (shared-memory atomics) into
-//                 the upper triangle of the row's F x F matrix, written out symmetric
-//                 with a zero diagonal.
+//   k_iv_fold     (depth <= 6) the four leaves of every bottom subtree folded per entry
+//                 into one vector of slot-pair values, as the values' k_fold does;
+//   k_iv_pack     (deeper trees) s2 per (leaf row, p_c) as PP contiguous floats;
+//   k_explain_iv_fold / k_explain_iv  one block per consumer row: the row's decision
+//                 codes, every tree's decision words, then per tree (folded: one gather
+//                 per live bottom subtree, the pairs of nodes above the bottom subtrees
+//                 summed in registers) or per live leaf the pair values added
+//                 (shared-memory atomics) into the upper triangle of the row's F x F
+//                 matrix, written out symmetric with a zero diagonal.
 // Unlike the values, the additions into one matrix element come from many threads,
 // so their order (and the last bits of the FP32 result) can change from run to run.
 #include <algorithm>
@@ -104,6 +107,65 @@ cudaError_t launch_iv_pack(int D, int PP, const float *S2, int n_live, float *S2
     const int64_t total = (int64_t)n_live << D;
     if (total == 0) return cudaSuccess;
     k_iv_pack<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(D, PP, S2, n_live, S2T);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---- folded form for trees of depth <= 6 ----
+// The four leaves of a bottom subtree share their path above the subtree root r.  Slots
+// of a subtree: 0..D-3 the ancestors of r (root first), D-2 = r, D-1 = its left child,
+// D = its right child.  A folded vector holds, per entry, the pair values of every slot
+// pair (u, v), u < v, except (left child, right child) (never on one path), summed
+// over the four leaves: IV_FP(D) = C(D+1, 2) - 1 values, padded to a multiple of 4.
+__host__ __device__ constexpr int iv_fp(int D) { return (D + 1) * D / 2 - 1; }
+__host__ __device__ constexpr int iv_fpp(int D) { return (iv_fp(D) + 3) & ~3; }
+// index of slot pair (u, v), u < v, in a folded vector (pairs ordered by u, then v)
+__host__ __device__ constexpr int iv_pidx(int D, int u, int v) {
+    return u * D - u * (u - 1) / 2 + (v - u - 1);
+}
+
+// One thread per (tree, bottom subtree, entry): fold the per-leaf pair values S2 [leaf
+// row][q * 2^D + p] of the subtree's four leaves (q over the leaf's position pairs).
+__global__ void k_iv_fold(int D, const float *__restrict__ S2, const int32_t *__restrict__ leaf_row, int T,
+                          float *__restrict__ fold) {
+    const int NS = 1 << (D - 2), E = 1 << (D + 1), NL = 1 << D, K = 1 << D, P = D * (D - 1) / 2;
+    const int FPP = iv_fpp(D);
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)T * NS * E) return;
+    const int e = (int)(idx % E);
+    const int s = (int)((idx / E) % NS);
+    const int t = (int)(idx / ((int64_t)E * NS));
+    const uint32_t pp = ((uint32_t)e >> 3) ^ (uint32_t)s, dn = (e >> 2) & 1, dnl = e & 1, dnr = (e >> 1) & 1;
+    float out[20];
+#pragma unroll
+    for (int k = 0; k < 20; ++k) out[k] = 0.0f;
+    for (int j = 0; j < 4; ++j) {
+        const int row = __ldg(leaf_row + (size_t)t * NL + 4 * s + j);
+        if (row < 0) continue;
+        const uint32_t fn = (j < 2) ? dn : (dn ^ 1u);
+        const uint32_t dch = (j < 2) ? dnl : dnr;
+        const uint32_t fc = ((j & 1) == 0) ? dch : (dch ^ 1u);
+        const uint32_t p = (pp << 2) | (fn << 1) | fc;
+        const float *Sr = S2 + (size_t)row * ((size_t)P << D);
+        int q = 0;
+        for (int k1 = 0; k1 < D; ++k1)
+            for (int k2 = k1 + 1; k2 < D; ++k2, ++q) {
+                // path position D-1 is the child of r on this leaf's path
+                const int u = k1, v = (k2 == D - 1 && j >= 2) ? D : k2;
+                out[iv_pidx(D, u, v)] += __ldg(Sr + ((size_t)q << D) + p);
+            }
+    }
+    (void)K;
+    float *dst = fold + idx * FPP;
+    for (int k = 0; k < FPP; ++k) dst[k] = out[k];
+}
+
+size_t iv_fold_floats(int D, int T) { return D <= 6 ? ((size_t)T << (D - 2 + D + 1)) * iv_fpp(D) : 0; }
+
+cudaError_t launch_iv_fold(int D, const float *S2, const int32_t *leaf_row, int T, float *fold, cudaStream_t st) {
+    if (D > 6) return cudaErrorInvalidValue;
+    const int64_t total = (int64_t)T << (D - 2 + D + 1);
+    k_iv_fold<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(D, S2, leaf_row, T, fold);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -224,6 +286,136 @@ __global__ void __launch_bounds__(kIvThreads) k_explain_iv(const float *__restri
     }
 }
 
+// Folded consumer kernel (depth <= 6): as k_explain_iv, but after the decision words a
+// thread takes a whole tree: per live bottom subtree one gathered folded vector, whose
+// pairs with r or its children go straight into the triangle, while the pairs of two
+// nodes above the bottom subtrees accumulate in registers (one per (node, ancestor))
+// and are added once per tree.
+template <int D, bool SMEM>
+__global__ void __launch_bounds__(kIvThreads) k_explain_iv_fold(const float *__restrict__ C, int64_t n, int64_t ldc,
+                                                              int F, TreeArrays ta, int T,
+                                                              const float *__restrict__ fold, float *__restrict__ out,
+                                                              int64_t ldo) {
+    using S = Shape<D>;
+    constexpr int NW = S::NW, NI = S::NI, NS = S::NS, E = S::E;
+    constexpr int FPP = iv_fpp(D);
+    // (node, ancestor) pairs above the bottom subtrees: node v of depth d has d of them
+    constexpr int UP = (D - 4) * (1 << (D - 2)) + 2 > 1 ? (D - 4) * (1 << (D - 2)) + 2 : 1;  // sum of depths, nodes 0..NS-2
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ncol = ta.n_cols, cshift = ta.code_bytes == 1 ? 5 : 6;
+    int *scode = reinterpret_cast<int *>(smem_raw);
+    uint32_t *sdw = reinterpret_cast<uint32_t *>(smem_raw + iv_up16((size_t)ncol * 4));
+    float *acc = reinterpret_cast<float *>(smem_raw + iv_up16((size_t)ncol * 4) + iv_up16((size_t)T * NW * 4));
+    const int tid = threadIdx.x;
+    const int64_t ntri = (int64_t)F * (F - 1) / 2;
+    for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
+        float *orow = out + row * ldo;
+        if (SMEM) {
+            for (int64_t k = tid; k < ntri; k += kIvThreads) acc[k] = 0.0f;
+        } else {
+            for (int64_t k = tid; k < (int64_t)F * F; k += kIvThreads) orow[k] = 0.0f;
+        }
+        const float *x = C + row * ldc;
+        for (int c = tid; c < ncol; c += kIvThreads) {
+            const int4 cv = __ldg(reinterpret_cast<const int4 *>(ta.cols) + c);
+            const CodeCol col{cv.x, cv.y, cv.z, cv.w};
+            scode[c] = decision_code(__ldg(x + col.feature), ta.col_thr + col.first, col);
+        }
+        __syncthreads();
+        for (int t = tid; t < T; t += kIvThreads) {
+            const TreeMeta m = load_meta(ta.meta + t);
+            const int4 *rec = reinterpret_cast<const int4 *>(ta.rec) + (size_t)t * NI;
+            uint32_t lo = 0u, hi = 0u;
+            for (int i = 0; i < m.wend[NW - 1]; ++i) {
+                const int4 r = __ldg(rec + i);
+                const uint32_t s = 0u - (uint32_t)(scode[r.x >> cshift] <= r.y);
+                lo |= (uint32_t)r.z & s;
+                hi |= (uint32_t)r.w & s;
+            }
+            sdw[t * NW] = m.pt[0] | lo;
+            if (NW == 2) sdw[t * NW + 1] = m.pt[1] | hi;
+        }
+        __syncthreads();
+        auto add = [&](int fa, int fb, float v) {
+            const int a = min(fa, fb), b = max(fa, fb);
+            if (v != 0.0f && b < F && a != b) {
+                if (SMEM)
+                    atomicAdd(acc + iv_tri(a, b, F), v);
+                else
+                    atomicAdd(orow + (size_t)a * F + b, v);
+            }
+        };
+        for (int t = tid; t < T; t += kIvThreads) {
+            uint32_t dw[NW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) dw[w] = sdw[t * NW + w];
+            uint32_t ent[NS];
+            subtree_entries<D>(dw, ent);
+            const uint64_t lv = __ldg(&ta.meta[t].live);
+            const int2 *nd = ta.nodes + (size_t)t * NI;
+            float up[UP];
+#pragma unroll
+            for (int k = 0; k < UP; ++k) up[k] = 0.0f;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                if (!((lv >> s) & 1ull)) continue;
+                const int r = NS - 1 + s;
+                const float4 *src = reinterpret_cast<const float4 *>(fold + (((size_t)t * NS + s) * E + ent[s]) * FPP);
+                float v[FPP];
+#pragma unroll
+                for (int u = 0; u < FPP / 4; ++u) {
+                    const float4 w4 = __ldg(src + u);
+                    v[4 * u] = w4.x; v[4 * u + 1] = w4.y; v[4 * u + 2] = w4.z; v[4 * u + 3] = w4.w;
+                }
+                int fs[D + 1];  // features of the slots
+#pragma unroll
+                for (int k = 0; k < D - 2; ++k) fs[k] = __ldg(&nd[((r + 1) >> (D - 2 - k)) - 1].x);
+                fs[D - 2] = __ldg(&nd[r].x);
+                fs[D - 1] = __ldg(&nd[2 * r + 1].x);
+                fs[D] = __ldg(&nd[2 * r + 2].x);
+                // pairs of two ancestors: into the (node, ancestor) registers
+#pragma unroll
+                for (int kv = 1; kv < D - 2; ++kv) {
+                    const int hv = ((r + 1) >> (D - 2 - kv)) - 1;  // ancestor at depth kv
+                    // registers of node hv start at the sum of depths of nodes 0..hv-1
+                    int base = 0;
+#pragma unroll
+                    for (int h = 0; h < NS - 1; ++h) base += h < hv ? 31 - __clz(h + 1) : 0;
+#pragma unroll
+                    for (int ku = 0; ku < kv; ++ku) up[base + ku] += v[iv_pidx(D, ku, kv)];
+                }
+                // pairs with r or one of its children: straight into the matrix
+#pragma unroll
+                for (int u = 0; u <= D - 2; ++u)
+#pragma unroll
+                    for (int w = (u < D - 2 ? D - 2 : D - 1); w <= D; ++w)
+                        if (u < w) add(fs[u], fs[w], v[iv_pidx(D, u, w)]);
+            }
+            // the (node, ancestor) pairs above the bottom subtrees, once per tree
+            int k = 0;
+#pragma unroll
+            for (int h = 1; h < NS - 1; ++h) {
+                const int dh = 31 - __clz(h + 1);  // depth of node h
+                const int fh = __ldg(&nd[h].x);
+#pragma unroll
+                for (int ku = 0; ku < dh; ++ku, ++k) {
+                    const int anc = ((h + 1) >> (dh - ku)) - 1;
+                    add(__ldg(&nd[anc].x), fh, up[k]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int64_t k = tid; k < (int64_t)F * F; k += kIvThreads) {
+            const int i = (int)(k / F), j = (int)(k - (int64_t)i * F);
+            if (SMEM)
+                orow[k] = i == j ? 0.0f : acc[iv_tri(min(i, j), max(i, j), F)];
+            else if (i > j)
+                orow[k] = orow[(size_t)j * F + i];
+        }
+        __syncthreads();
+    }
+}
+
 size_t iv_smem_bytes(int D, int F, int T, int n_cols, bool smem_acc) {
     const int NW = ((1 << D) - 1 + 31) / 32;
     return iv_up16((size_t)n_cols * 4) + iv_up16((size_t)T * NW * 4) +
@@ -232,44 +424,60 @@ size_t iv_smem_bytes(int D, int F, int T, int n_cols, bool smem_acc) {
 
 template <int D, bool SMEM>
 static cudaError_t iv_t(const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
-                        const int32_t *group_leaf, int n_live, const float *S2T, float *out, int64_t ldo,
-                        const DevInfo &dev, cudaStream_t st) {
+                        const int32_t *group_leaf, int n_live, const float *S2T, const float *fold, float *out,
+                        int64_t ldo, const DevInfo &dev, cudaStream_t st) {
     const size_t smem = iv_smem_bytes(D, F, T, ta.n_cols, SMEM);
     if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
-    auto kern = k_explain_iv<D, SMEM>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kIvThreads, smem);
-    if (err != cudaSuccess) return err;
-    const int64_t grid = std::min<int64_t>(n, (int64_t)dev.sms * std::max(per_sm, 1));
-    kern<<<(unsigned)grid, kIvThreads, smem, st>>>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo);
+    cudaError_t err;
+    const int64_t cap = n;
+    bool done = false;
+    if constexpr (D <= 6) {
+        if (fold != nullptr) {
+            auto kern = k_explain_iv_fold<D, SMEM>;
+            err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err == cudaSuccess)
+                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kIvThreads, smem);
+            if (err != cudaSuccess) return err;
+            const int64_t grid = std::min<int64_t>(cap, (int64_t)dev.sms * std::max(per_sm, 1));
+            kern<<<(unsigned)grid, kIvThreads, smem, st>>>(C, n, ldc, F, ta, T, fold, out, ldo);
+            done = true;
+        }
+    }
+    if (!done) {
+        auto kern = k_explain_iv<D, SMEM>;
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kIvThreads, smem);
+        if (err != cudaSuccess) return err;
+        const int64_t grid = std::min<int64_t>(cap, (int64_t)dev.sms * std::max(per_sm, 1));
+        kern<<<(unsigned)grid, kIvThreads, smem, st>>>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo);
+    }
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int D>
 static cudaError_t iv_d(const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
-                        const int32_t *group_leaf, int n_live, const float *S2T, float *out, int64_t ldo,
-                        const DevInfo &dev, cudaStream_t st) {
+                        const int32_t *group_leaf, int n_live, const float *S2T, const float *fold, float *out,
+                        int64_t ldo, const DevInfo &dev, cudaStream_t st) {
     // the triangle in shared memory while two blocks still fit per SM, else in place
     if (iv_smem_bytes(D, F, T, ta.n_cols, true) <= dev.smem_optin / 2)
-        return iv_t<D, true>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
-    return iv_t<D, false>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+        return iv_t<D, true>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, fold, out, ldo, dev, st);
+    return iv_t<D, false>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, fold, out, ldo, dev, st);
 }
 
 cudaError_t launch_explain_iv(int D, const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
-                              const int32_t *group_leaf, int n_live, const float *S2T, float *out, int64_t ldo,
-                              const DevInfo &dev, cudaStream_t st) {
+                              const int32_t *group_leaf, int n_live, const float *S2T, const float *fold, float *out,
+                              int64_t ldo, const DevInfo &dev, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     switch (D) {
-        case 2: return iv_d<2>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
-        case 3: return iv_d<3>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
-        case 4: return iv_d<4>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
-        case 5: return iv_d<5>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
-        case 6: return iv_d<6>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
-        case 7: return iv_d<7>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
-        case 8: return iv_d<8>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, out, ldo, dev, st);
+        case 2: return iv_d<2>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, fold, out, ldo, dev, st);
+        case 3: return iv_d<3>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, fold, out, ldo, dev, st);
+        case 4: return iv_d<4>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, fold, out, ldo, dev, st);
+        case 5: return iv_d<5>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, fold, out, ldo, dev, st);
+        case 6: return iv_d<6>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, fold, out, ldo, dev, st);
+        case 7: return iv_d<7>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, fold, out, ldo, dev, st);
+        case 8: return iv_d<8>(C, n, ldc, F, ta, T, group_leaf, n_live, S2T, fold, out, ldo, dev, st);
         default: return cudaErrorInvalidValue;
     }
 }
