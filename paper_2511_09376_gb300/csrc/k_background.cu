@@ -22,6 +22,50 @@
 
 namespace wdf {
 
+// 16-bit counter slots in shared memory.  The rows of one warp increment the entries of
+// one (tree, subtree) together, and background entries are far from uniform (a warp's
+// most frequent entry is hit by about a quarter of its lanes), so lanes that land in
+// one bank serialise.  Two rules spread them: the two halves of a 32-bit word hold the
+// same entry of two sibling subtrees (so one instruction touches one entry per word),
+// and the word of entry e within its subtree pair is fold(e), which XORs the higher
+// entry bits into the five bank bits.  fold is its own inverse (bits 5 and up pass
+// through unchanged).
+__host__ __device__ __forceinline__ uint32_t bg_fold(uint32_t e) {
+    return e ^ ((e >> 5) & 31u) ^ ((e >> 10) & 31u);
+}
+
+template <int D>
+__device__ __forceinline__ uint32_t bg_slot(int g, int s, uint32_t e) {
+    using S = Shape<D>;
+    if constexpr (S::NS == 1)
+        return (uint32_t)g * S::E + e;
+    else
+        return (((uint32_t)g * (S::NS / 2) + (uint32_t)(s >> 1)) * S::E + bg_fold(e)) * 2u + (uint32_t)(s & 1);
+}
+
+// Adds the shared counters of a block's trees into the global 32-bit counts ([tree]
+// [subtree][entry], gdst at the block's first tree) and zeroes them.
+template <int D>
+__device__ void bg_flush(uint32_t *sh, uint32_t *gdst, int bins, int tid, int nthreads) {
+    using S = Shape<D>;
+    for (int i = tid; i < bins / 2; i += nthreads) {
+        const uint32_t v = sh[i];
+        sh[i] = 0u;
+        if (!v) continue;
+        size_t i0, i1;
+        if constexpr (S::NS == 1) {
+            i0 = 2 * (size_t)i;
+            i1 = i0 + 1;
+        } else {
+            const uint32_t pair = (uint32_t)i / S::E, e = bg_fold((uint32_t)i % S::E);
+            i0 = (size_t)(2 * pair) * S::E + e;  // subtree 2k of the pair; 2k + 1 is E further
+            i1 = i0 + S::E;
+        }
+        if (v & 0xFFFFu) atomicAdd(gdst + i0, v & 0xFFFFu);
+        if (v >> 16) atomicAdd(gdst + i1, v >> 16);
+    }
+}
+
 // Shared memory layout (bytes, 16-aligned pieces): code tile | tree metadata | node
 // records | 16-bit counters.
 template <int D>
@@ -65,12 +109,7 @@ __global__ void __launch_bounds__(RT) k_bg_hist(const unsigned char *__restrict_
     for (int64_t row0 = (int64_t)slice * RT; row0 < m; row0 += (int64_t)nslices * RT) {
         __syncthreads();
         if (SMEM && since_flush + RT > 65535) {  // a 16-bit counter could overflow: flush
-            for (int i = tid; i < bins / 2; i += RT) {
-                const uint32_t v = sh[i];
-                if (v & 0xFFFFu) atomicAdd(gdst + 2 * i, v & 0xFFFFu);
-                if (v >> 16) atomicAdd(gdst + 2 * i + 1, v >> 16);
-                sh[i] = 0u;
-            }
+            bg_flush<D>(sh, gdst, bins, tid, RT);
             since_flush = 0;
         }
         // the tile's RT rows are RT / 32 consecutive code blocks
@@ -92,22 +131,19 @@ __global__ void __launch_bounds__(RT) k_bg_hist(const unsigned char *__restrict_
 #pragma unroll
             for (int s = 0; s < S::NS; ++s) {
                 if (((lv >> s) & 1ull) && valid) {
-                    const uint32_t idx = (uint32_t)(g * S::NS + s) * S::E + ent[s];
-                    if (SMEM)
-                        atomicAdd(sh + (idx >> 1), 1u << ((idx & 1u) << 4));
-                    else
-                        atomicAdd(gdst + idx, 1u);
+                    if (SMEM) {
+                        const uint32_t sl = bg_slot<D>(g, s, ent[s]);
+                        atomicAdd(sh + (sl >> 1), 1u << ((sl & 1u) << 4));
+                    } else {
+                        atomicAdd(gdst + (uint32_t)(g * S::NS + s) * S::E + ent[s], 1u);
+                    }
                 }
             }
         }
     }
     if (SMEM) {
         __syncthreads();
-        for (int i = tid; i < bins / 2; i += RT) {
-            const uint32_t v = sh[i];
-            if (v & 0xFFFFu) atomicAdd(gdst + 2 * i, v & 0xFFFFu);
-            if (v >> 16) atomicAdd(gdst + 2 * i + 1, v >> 16);
-        }
+        bg_flush<D>(sh, gdst, bins, tid, RT);
     }
 }
 
