@@ -51,7 +51,11 @@ typedef enum {
 typedef enum {
     WDF_FP32 = 0,    /* FP32 operands, FP32 accumulation (CUDA cores) */
     WDF_TF32X3 = 1,  /* TF32 hi+lo split operands, three tensor-core products, FP32 accumulation */
-    WDF_BF16X3 = 2   /* BF16 hi+lo split operands, three tensor-core products, FP32 accumulation */
+    WDF_BF16X3 = 2,  /* BF16 hi+lo split operands, three tensor-core products, FP32 accumulation
+                        (16 significant bits per operand: relative error about 2^-16 where a
+                        background count exceeds 2^16 or a table value needs more bits) */
+    WDF_BF16X6 = 3   /* BF16 hi+mid+lo split operands (exact for every FP32 value), the six
+                        tensor-core products of total order <= 2, FP32 accumulation: FP32 accuracy */
 } wdf_precision;
 
 typedef enum { WDF_MEM_HOST = 0, WDF_MEM_DEVICE = 1 } wdf_memkind;
@@ -102,7 +106,7 @@ wdf_status wdf_ensemble_info(const wdf_ensemble *ens, wdf_info *out);
  * decision codes pass through a buffer the ensemble keeps (up to 2^20 rows of codes).
  * Calls on one ensemble must not overlap on the GPU.
  * WDF_EUNSUPPORTED: m == 0 (an empty background is the path-dependent variant).
- * precision WDF_TF32X3 / WDF_BF16X3 runs the contraction on the tensor cores (tcgen05,
+ * precision WDF_TF32X3 / WDF_BF16X3 / WDF_BF16X6 runs the contraction on the tensor cores (tcgen05,
  * TMEM accumulators) and then waits for the stream to check the kernel's bounded waits:
  * WDF_ETIMEOUT if one expired.  WDF_FP32 is stream-ordered without waiting; a later
  * wdf_explain on the same stream sees the result.

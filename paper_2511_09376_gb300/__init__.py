@@ -8,6 +8,7 @@ library.  If the library has not been built, importing the binding raises.
 """
 from ._binding import (  # noqa: F401
     BF16X3,
+    BF16X6,
     Batch,
     batch_autotune,
     batch_create,

@@ -14,8 +14,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libwoodelf.so")
 
-FP32, TF32X3, BF16X3 = 0, 1, 2
-_PRECISION = {"fp32": FP32, "tf32x3": TF32X3, "bf16x3": BF16X3}
+FP32, TF32X3, BF16X3, BF16X6 = 0, 1, 2, 3
+_PRECISION = {"fp32": FP32, "tf32x3": TF32X3, "bf16x3": BF16X3, "bf16x6": BF16X6}
 _METRIC = {"shapley": 0, "banzhaf": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
 

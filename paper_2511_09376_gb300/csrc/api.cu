@@ -179,6 +179,13 @@ cudaError_t copy_rows(float *dst, int64_t ldd, const float *src, int64_t lds, in
     return cudaMemcpy2DAsync(dst, (size_t)ldd * 4, src, (size_t)lds * 4, (size_t)F * 4, (size_t)rows, kind, st);
 }
 
+bool valid_precision(wdf_precision p) {
+    return p == WDF_FP32 || p == WDF_TF32X3 || p == WDF_BF16X3 || p == WDF_BF16X6;
+}
+
+// The tensor-core kernel's operand split: 0 = TF32 two parts, 1 = BF16 two, 2 = BF16 three.
+int tc_mode(wdf_precision p) { return p == WDF_TF32X3 ? 0 : (p == WDF_BF16X3 ? 1 : 2); }
+
 // Buffers of the consumer-independent half (counts, frequencies, S, folded vectors) and,
 // for the tensor-core precisions, the K-major tables.
 wdf_status ensure_frequency_state(wdf_ensemble *ens, wdf_precision precision) {
@@ -208,7 +215,7 @@ wdf_status contract_and_fold(wdf_ensemble *ens, wdf_precision precision, cudaStr
         WDF_CUDA(wdf::launch_contract_fp32(p.D, ens->d_A, ens->d_scale, ens->d_tiles, ens->n_tiles, ens->d_t32,
                                            ens->d_S, st));
     } else {
-        WDF_CUDA(wdf::launch_contract_tc(p.D, precision == WDF_BF16X3 ? 1 : 0, ens->d_A, ens->d_scale,
+        WDF_CUDA(wdf::launch_contract_tc(p.D, tc_mode(precision), ens->d_A, ens->d_scale,
                                          ens->d_tiles128, ens->n_tiles128, ens->d_t32t, ens->d_S, ens->d_err, st));
         // a bounded wait inside the kernel that expired is reported here
         int flag = 0;
@@ -392,7 +399,7 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
     if (ldb < ens->pk.F) return fail(WDF_EINVAL, "ldb < n_features");
     if (m > (int64_t)0xFFFFFFFF) return fail(WDF_EUNSUPPORTED, "more than 2^32-1 background rows");
     if (kind != WDF_MEM_HOST && kind != WDF_MEM_DEVICE) return fail(WDF_EINVAL, "bad memory kind");
-    if (precision != WDF_FP32 && precision != WDF_TF32X3 && precision != WDF_BF16X3)
+    if (!valid_precision(precision))
         return fail(WDF_EINVAL, "unknown precision");
     DeviceGuard g(ens->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -463,7 +470,7 @@ wdf_status wdf_set_background_counts(wdf_ensemble *ens, const uint32_t *counts, 
     if (!counts) return fail(WDF_EINVAL, "counts is null");
     if (m_total < 1) return fail(WDF_EUNSUPPORTED, "empty background (m_total < 1)");
     if (m_total > (int64_t)0xFFFFFFFF) return fail(WDF_EUNSUPPORTED, "more than 2^32-1 background rows");
-    if (precision != WDF_FP32 && precision != WDF_TF32X3 && precision != WDF_BF16X3)
+    if (!valid_precision(precision))
         return fail(WDF_EINVAL, "unknown precision");
     DeviceGuard g(ens->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -491,7 +498,7 @@ wdf_status wdf_set_covers(wdf_ensemble *ens, const double *cover) {
 wdf_status wdf_set_path_dependent(wdf_ensemble *ens, wdf_precision precision, void *stream) {
     if (!ens) return fail(WDF_EINVAL, "ens is null");
     if (!ens->has_covers) return fail(WDF_EINVAL, "wdf_set_covers must succeed before wdf_set_path_dependent");
-    if (precision != WDF_FP32 && precision != WDF_TF32X3 && precision != WDF_BF16X3)
+    if (!valid_precision(precision))
         return fail(WDF_EINVAL, "unknown precision");
     DeviceGuard g(ens->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;

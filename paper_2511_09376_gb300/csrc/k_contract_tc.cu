@@ -1,9 +1,13 @@
 // Step 3 of Algorithm 3 on the 5th-generation tensor cores: the stacked contraction
 // S[row][k * 2^D + p_c] = scale[row] * sum_p A[row][p] * T[g][p][k * 2^D + p_c]
 // (Eq. "bg_shap_derivation" step (f) for every leaf of one path signature at once) with
-// split-precision operands: X = X_hi + X_lo, both halves rounded to TF32 (kind::tf32) or
-// BF16 (kind::f16), and three products A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in
-// FP32 in tensor memory.  The dropped A_lo B_lo term is below the rounding of the rest.
+// split-precision operands accumulated in FP32 in tensor memory.  Two-part splits
+// X = X_0 + X_1 (both parts rounded to TF32, kind::tf32, or to BF16, kind::f16) take
+// three products A_0 B_0 + A_0 B_1 + A_1 B_0; the dropped A_1 B_1 term is below the
+// rounding of the rest, so the result carries the parts' 2 x 11 (TF32) or 2 x 8 (BF16)
+// significant bits.  The three-part BF16 split X = X_0 + X_1 + X_2 holds every FP32
+// value exactly (3 x 8 bits) and takes the six products A_i B_j with i + j <= 2; the
+// dropped ones are below 2^-24 relative, FP32 accuracy.
 //
 // One CTA computes a 128-row tile of one signature group and up to 256 columns.  Operands
 // are converted while being staged into shared memory in the K-major, no-swizzle
@@ -89,23 +93,27 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k, int KC) {
     return (uint32_t)((row >> 3) * kcb * 128 + ((k * EB) >> 4) * 128 + (row & 7) * 16 + ((k * EB) & 15));
 }
 
-template <bool BF16>
-__device__ __forceinline__ void put_split(unsigned char *hi, unsigned char *lo, uint32_t off, float x) {
-    if (BF16) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-        *reinterpret_cast<__nv_bfloat16 *>(hi + off) = h;
-        *reinterpret_cast<__nv_bfloat16 *>(lo + off) = l;
-    } else {
-        const float h = tf32_rna(x);
-        *reinterpret_cast<float *>(hi + off) = h;
-        *reinterpret_cast<float *>(lo + off) = tf32_rna(x - h);
+// Writes the NP parts of x, part j at part[0] + j * stride.  Each remainder x - sum of
+// the earlier parts is exact in FP32 (the parts are x's leading bits).
+template <bool BF16, int NP>
+__device__ __forceinline__ void put_split(unsigned char *part, uint32_t stride, uint32_t off, float x) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        if (BF16) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            *reinterpret_cast<__nv_bfloat16 *>(part + j * stride + off) = h;
+            x -= __bfloat162float(h);
+        } else {
+            const float h = tf32_rna(x);
+            *reinterpret_cast<float *>(part + j * stride + off) = h;
+            x -= h;
+        }
     }
 }
 
 }  // namespace
 
-template <bool BF16>
+template <bool BF16, int NP>
 __global__ void __launch_bounds__(128) k_contract_tc(int D, const float *__restrict__ A,
                                                      const float *__restrict__ scale, const int4 *__restrict__ tiles,
                                                      const float *__restrict__ t32t, float *__restrict__ S, int NT,
@@ -119,9 +127,9 @@ __global__ void __launch_bounds__(128) k_contract_tc(int D, const float *__restr
     const int g = tile.x, r0 = tile.y, r1 = tile.z;
     const int n0 = blockIdx.y * NT;
     const uint32_t a_bytes = (uint32_t)kRows * KC * EB, b_bytes = (uint32_t)NT * KC * EB;
-    unsigned char *a_hi = smem, *a_lo = smem + a_bytes;
-    unsigned char *b_hi = smem + 2 * a_bytes, *b_lo = b_hi + b_bytes;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(b_lo + b_bytes);
+    unsigned char *a_part = smem;                  // NP parts of the A tile, a_bytes apart
+    unsigned char *b_part = smem + NP * a_bytes;  // NP parts of the B tile, b_bytes apart
+    uint64_t *bar = reinterpret_cast<uint64_t *>(b_part + NP * b_bytes);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int ncols = 32;
@@ -148,13 +156,13 @@ __global__ void __launch_bounds__(128) k_contract_tc(int D, const float *__restr
             const int row = i / KC, k = i % KC;
             const int gr = r0 + row, gk = kc0 + k;
             const float x = (gr < r1 && gk < K) ? __ldg(A + ((size_t)gr << D) + gk) : 0.0f;
-            put_split<BF16>(a_hi, a_lo, tile_off<EB>(row, k, KC), x);
+            put_split<BF16, NP>(a_part, a_bytes, tile_off<EB>(row, k, KC), x);
         }
         for (int i = tid; i < NT * KC; i += 128) {
             const int col = i / KC, k = i % KC;
             const int gc = n0 + col, gk = kc0 + k;
             const float x = (gc < N && gk < K) ? __ldg(t32t + ((size_t)g * N + gc) * K + gk) : 0.0f;
-            put_split<BF16>(b_hi, b_lo, tile_off<EB>(col, k, KC), x);
+            put_split<BF16, NP>(b_part, b_bytes, tile_off<EB>(col, k, KC), x);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -163,14 +171,16 @@ __global__ void __launch_bounds__(128) k_contract_tc(int D, const float *__restr
             const uint32_t sbo_a = (uint32_t)(KC * EB / 16) * 128, sbo_b = sbo_a;
             for (int ks = 0; ks < KC; ks += KSTEP) {
                 const uint32_t koff = (uint32_t)(ks / KSTEP) * 256;
-                const uint64_t dah = smem_desc(smem_u32(a_hi) + koff, 128, sbo_a);
-                const uint64_t dal = smem_desc(smem_u32(a_lo) + koff, 128, sbo_a);
-                const uint64_t dbh = smem_desc(smem_u32(b_hi) + koff, 128, sbo_b);
-                const uint64_t dbl = smem_desc(smem_u32(b_lo) + koff, 128, sbo_b);
                 const uint32_t acc = (kc0 > 0 || ks > 0) ? 1u : 0u;
-                mma<BF16>(tmem, dah, dbh, idesc, acc);
-                mma<BF16>(tmem, dah, dbl, idesc, 1u);
-                mma<BF16>(tmem, dal, dbh, idesc, 1u);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+#pragma unroll
+                    for (int j = 0; i + j < NP; ++j) {
+                        const uint64_t da = smem_desc(smem_u32(a_part + i * a_bytes) + koff, 128, sbo_a);
+                        const uint64_t db = smem_desc(smem_u32(b_part + j * b_bytes) + koff, 128, sbo_b);
+                        mma<BF16>(tmem, da, db, idesc, (i + j) ? 1u : acc);
+                    }
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(bar)));
@@ -211,36 +221,32 @@ __global__ void __launch_bounds__(128) k_contract_tc(int D, const float *__restr
     }
 }
 
-size_t contract_tc_smem(int D, int bf16, int *NT, int *KC) {
+// mode: 0 = TF32 two parts, 1 = BF16 two parts, 2 = BF16 three parts.
+size_t contract_tc_smem(int D, int mode, int *NT, int *KC) {
     const int K = 1 << D, N = D << D;
     const int KP = K < 16 ? 16 : K;
     int nt = N < 256 ? N : 256;
     nt = (nt + 15) / 16 * 16;
-    const int eb = bf16 ? 2 : 4;
-    int kc = bf16 ? 128 : 64;  // 256 bytes of K per row per chunk
+    const int eb = mode ? 2 : 4, np = mode == 2 ? 3 : 2;
+    int kc = mode == 1 ? 128 : 64;  // 256 bytes of K per row and part (128 B with three parts)
     if (kc > KP) kc = KP;
     *NT = nt;
     *KC = kc;
-    return (size_t)2 * (kRows + nt) * kc * eb + 16;
+    return (size_t)np * (kRows + nt) * kc * eb + 16;
 }
 
-cudaError_t launch_contract_tc(int D, int bf16, const float *A, const float *scale, const int4 *tiles, int n_tiles,
+cudaError_t launch_contract_tc(int D, int mode, const float *A, const float *scale, const int4 *tiles, int n_tiles,
                                const float *t32t, float *S, int *err, cudaStream_t st) {
     if (n_tiles == 0) return cudaSuccess;
+    if (mode < 0 || mode > 2) return cudaErrorInvalidValue;
     int NT = 0, KC = 0;
-    const size_t smem = contract_tc_smem(D, bf16, &NT, &KC);
+    const size_t smem = contract_tc_smem(D, mode, &NT, &KC);
     const int N = D << D;
     dim3 grid(n_tiles, (N + NT - 1) / NT);
-    cudaError_t e;
-    if (bf16) {
-        e = cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_contract_tc<true><<<grid, 128, smem, st>>>(D, A, scale, tiles, t32t, S, NT, KC, err);
-    } else {
-        e = cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_contract_tc<false><<<grid, 128, smem, st>>>(D, A, scale, tiles, t32t, S, NT, KC, err);
-    }
+    auto kern = mode == 0 ? k_contract_tc<false, 2> : (mode == 1 ? k_contract_tc<true, 2> : k_contract_tc<true, 3>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 128, smem, st>>>(D, A, scale, tiles, t32t, S, NT, KC, err);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -80,10 +80,11 @@ cudaError_t launch_contract_fp32(int D, const float *A, const float *scale, cons
                                  const float *t32, float *S, cudaStream_t st, int slots = 0);
 
 // Step 3 on the tensor cores (tcgen05, TMEM accumulators): the same S as
-// launch_contract_fp32 from split-precision operands, TF32 (bf16 == 0) or BF16 (1).
+// launch_contract_fp32 from split-precision operands: mode 0 = TF32 hi+lo, 1 = BF16
+// hi+lo (three products each), 2 = BF16 hi+mid+lo (six products).
 // tiles: (group, row0, row_end, 0) work items of up to 128 rows; t32t the K-major tables.
 // err is set to 1 if a bounded wait expired.
-cudaError_t launch_contract_tc(int D, int bf16, const float *A, const float *scale, const int4 *tiles, int n_tiles,
+cudaError_t launch_contract_tc(int D, int mode, const float *A, const float *scale, const int4 *tiles, int n_tiles,
                                const float *t32t, float *S, int *err, cudaStream_t st);
 
 // Folds the per-leaf S rows of every bottom subtree into per-entry slot vectors

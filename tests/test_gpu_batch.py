@@ -13,7 +13,7 @@ SPECS = [  # (seed, n, m, F, n_gauss, T, depth, leaf_std, early_p, complete, pre
     (42, 0, 3000, 33, 20, 20, 4, 0.3, 0.1, False, "bf16x3"),
     (43, 0, 3000, 127, 90, 25, 6, 0.1, 0.1, False, "fp32"),
     (44, 0, 3000, 64, 40, 10, 6, 0.1, 0.1, False, "tf32x3"),
-    (45, 0, 3000, 50, 30, 8, 7, 0.1, 0.1, False, "bf16x3"),
+    (45, 0, 3000, 50, 30, 8, 7, 0.1, 0.1, False, "bf16x6"),
     (46, 0, 3000, 300, 200, 6, 8, 0.1, 0.1, False, "fp32"),
 ]
 

@@ -160,12 +160,19 @@ def test_phi_mid_full_background(wdf, ctx):
     assert_phi_close(phi2, p1)
 
 
-def test_phi_large_sampled_rows(wdf, ctx):
-    """The large workload at full size (3e6 consumers, 5e6 background rows, 200 trees),
-    launched as the benchmark launches it; sampled consumers against the oracle with
-    the full background counts."""
-    import torch
+@pytest.fixture(scope="module")
+def large():
+    """The large workload (3e6 consumers, 5e6 background rows, 127 features, 200 trees of
+    depth 6) and the oracle's background counts of all 5e6 rows."""
     ens, C, B = synth.make("large")
+    return ens, C, B, oracle.bg_hist(ens, B)
+
+
+def test_phi_large_sampled_rows(wdf, ctx, large):
+    """The large workload at full size, launched as the benchmark launches it; sampled
+    consumers against the oracle with the full background counts."""
+    import torch
+    ens, C, B, counts = large
     e = wdf.load_ensemble(ctx, ens)
     dB = _dev(B)
     wdf.set_background(e, dB)
@@ -176,13 +183,39 @@ def test_phi_large_sampled_rows(wdf, ctx):
     rows = np.unique(np.concatenate([np.linspace(0, C.shape[0] - 1, 48).astype(np.int64),
                                      [0, 63, 64, C.shape[0] - 1], seams]))
     got = phi[torch.from_numpy(rows).to(phi.device)].cpu().numpy()
-    counts = oracle.bg_hist(ens, B)
     want = oracle.values_hist(ens, counts, B.shape[0], C[rows])
     assert_phi_close(got, want)
     assert wdf.expected_value(e) == pytest.approx(oracle.base_from_hist(ens, counts, B.shape[0]), rel=1e-9)
     # background counts at full size, bit-exact for every leaf
     _check_counts(wdf, e, ens, B, counts)
     del phi, dC
+
+
+@pytest.fixture(scope="module")
+def large_sample(large):
+    """10,000 seeded consumer rows of the large workload and their oracle values."""
+    ens, C, B, counts = large
+    rows = np.sort(np.random.default_rng(2511).choice(C.shape[0], 10_000, replace=False))
+    return C[rows], oracle.values_hist(ens, counts, B.shape[0], C[rows])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16x3", "bf16x6"])
+def test_large_contraction_precisions(wdf, ctx, large, large_sample, precision):
+    """Every contraction precision on the full large background, error against the FP64
+    oracle on a 10,000-consumer sample.  Counts here reach 4.8e6 (23 bits): FP32, TF32
+    hi+lo (22 bits per operand) and BF16 hi+mid+lo (24 bits) meet the FP32-mode bound;
+    BF16 hi+lo keeps 16 bits of each count and table value (relative error up to about
+    2^-16 per product) and is held to a tenfold looser bound."""
+    ens, C, B, counts = large
+    Cs, want = large_sample
+    e = wdf.load_ensemble(ctx, ens)
+    wdf.set_background(e, _dev(B), precision)
+    got = wdf.explain(e, _dev(Cs)).cpu().numpy().astype(np.float64)
+    err = np.abs(got - want)
+    scale = 10.0 if precision == "bf16x3" else 1.0
+    bound = scale * (ATOL + RTOL * np.abs(want))
+    assert (err <= bound).all(), f"{precision}: max |err| {err.max():.3e}, worst ratio {(err / bound).max():.3f}"
+    e.close()
 
 
 # ------------------------------------------------------------------ edge cases
@@ -290,6 +323,9 @@ def test_empty_and_error_paths(wdf, ctx):
     with pytest.raises(wdf.WdfError) as ei:
         wdf.set_background(e, _dev(B[:0]))
     assert ei.value.status == 4
+    with pytest.raises(wdf.WdfError) as ei:
+        wdf.set_background(e, _dev(B), 4)  # no such precision
+    assert ei.value.status == 1
     wdf.set_background(e, _dev(B))
     out = wdf.explain(e, _dev(C[:0]))
     assert out.shape == (0, ens.n_features)

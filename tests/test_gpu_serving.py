@@ -10,7 +10,7 @@ from paper_2511_09376_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 SPECS = [(51, 2000, 30, 20, 25, 4, 0.3, 0.1, False, "fp32"),
-         (52, 2000, 127, 90, 40, 6, 0.1, 0.1, False, "bf16x3"),
+         (52, 2000, 127, 90, 40, 6, 0.1, 0.1, False, "bf16x6"),
          (53, 2000, 60, 40, 12, 7, 0.1, 0.1, False, "tf32x3")]
 
 
