@@ -82,7 +82,7 @@ namespace {
 void free_ensemble(wdf_ensemble *e) {
     dfree(e->d_nodes); dfree(e->d_keys); dfree(e->d_group_leaf); dfree(e->d_leaf_row);
     dfree(e->d_w_rows); dfree(e->d_tiles); dfree(e->d_t32);
-    dfree(e->d_rec); dfree(e->d_meta); dfree(e->d_cols); dfree(e->d_col_thr); dfree(e->d_zero);
+    dfree(e->d_rec); dfree(e->d_meta); dfree(e->d_cols); dfree(e->d_col_thr);
     dfree(e->d_t32t); dfree(e->d_tiles128); dfree(e->d_err); dfree(e->d_A); dfree(e->d_ratio);
     dfree(e->d_hist); dfree(e->d_vc); dfree(e->d_scale); dfree(e->d_S); dfree(e->d_sfold); dfree(e->d_base);
     for (int i = 0; i < 2; ++i) {
@@ -322,7 +322,6 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
     chk(dalloc(&e->d_meta, p.meta.size(), &e->bytes));
     chk(dalloc(&e->d_cols, p.cols.size(), &e->bytes));
     chk(dalloc(&e->d_col_thr, std::max<size_t>(p.col_thr.size(), 1), &e->bytes));
-    chk(dalloc(&e->d_zero, 16, &e->bytes));
     if (ce == cudaSuccess) {
         chk(cudaMemcpy(e->d_nodes, nodes.data(), nodes.size() * sizeof(int2), cudaMemcpyHostToDevice));
         if (e->G) chk(cudaMemcpy(e->d_keys, p.sig_key.data(), p.sig_key.size() * 4, cudaMemcpyHostToDevice));
@@ -336,7 +335,6 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
         chk(cudaMemcpy(e->d_cols, p.cols.data(), p.cols.size() * sizeof(wdf::CodeCol), cudaMemcpyHostToDevice));
         if (!p.col_thr.empty())
             chk(cudaMemcpy(e->d_col_thr, p.col_thr.data(), p.col_thr.size() * 4, cudaMemcpyHostToDevice));
-        chk(cudaMemset(e->d_zero, 0, 16 * sizeof(float)));
         if (e->n_tiles) chk(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
         // step 2 of Algorithm 3 depends only on the path signatures: build the tables now
         chk(wdf::launch_tables(p.D, e->metric, e->d_keys, e->G, e->d_t32, nullptr, nullptr, 0));

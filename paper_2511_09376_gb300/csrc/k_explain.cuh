@@ -6,14 +6,14 @@
 // nodes of a chunk of trees.  Per tree the thread evaluates those nodes (decision
 // bitmask in registers), forms its entry at every bottom subtree, and gathers one slot
 // vector per subtree from the folded table -- all gathers of a group of subtrees are
-// issued before any is used, so their L2 latency overlaps; a dead subtree reads a zero
-// row instead.  The slots of the nodes above the bottom subtrees
+// issued before any is used, so their L2 latency overlaps; a dead subtree issues no load
+// (its slots are zero).  The slots of the nodes above the bottom subtrees
 // accumulate in registers (one per node, the node-level form of the NumPy indexing of
 // section "Algorithmic Improvements" item 6); every node's value is then added into
 // phi[feature of the node] in the fixed flush order of tree_layout.h, eight at a time:
 // a batch that repeats no feature reads its eight phi values before writing any, so
 // the shared-memory round trips overlap; any other batch adds one by one.  Pass-through
-// nodes add into a scratch row.  The order of every floating-point addition into a
+// nodes map to a scratch row and are skipped.  The order of every floating-point addition into a
 // row's phi depends only on the ensemble, never on which rows share a block.
 //
 // The kernels are templates of the depth; every depth is instantiated in its own
@@ -58,44 +58,52 @@ struct ExLayout {
     }
 };
 
-__device__ __forceinline__ float4 ldg_f4(const float4 *p) {
-    float4 r;
-    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-                 : "l"(p));
-    return r;
+// 16-byte and 32-byte read-only loads predicated on `on` (the outputs keep their values
+// when off): a dead bottom subtree issues no load, so it costs no L1 data-pipe wavefronts.
+__device__ __forceinline__ void ldg_f4_if(const float4 *p, float4 &r, uint32_t on) {
+    asm volatile(
+        "{\n.reg .pred q;\nsetp.ne.u32 q, %5, 0;\n@q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];\n}\n"
+        : "+f"(r.x), "+f"(r.y), "+f"(r.z), "+f"(r.w)
+        : "l"(p), "r"(on));
 }
 
 // One 32-byte entry in a single 256-bit load (the address is 32-byte aligned).
-__device__ __forceinline__ void ldg_f8(const float4 *p, float4 &a, float4 &b) {
-    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-                 : "l"(p));
+__device__ __forceinline__ void ldg_f8_if(const float4 *p, float4 &a, float4 &b, uint32_t on) {
+    asm volatile(
+        "{\n.reg .pred q;\nsetp.ne.u32 q, %9, 0;\n@q ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n}\n"
+        : "+f"(a.x), "+f"(a.y), "+f"(a.z), "+f"(a.w), "+f"(b.x), "+f"(b.y), "+f"(b.z), "+f"(b.w)
+        : "l"(p), "r"(on));
 }
 
 // phi[o[q]] += val[q], q < cnt, one after another: the rare batch that repeats a
 // feature.  Kept out of line so the per-tree loop stays small in the instruction cache.
-static __device__ __noinline__ void flush_serial(float *myphi, int4 oa, int4 ob, float4 va, float4 vb, int cnt) {
+static __device__ __noinline__ void flush_serial(float *myphi, int4 oa, int4 ob, float4 va, float4 vb, int cnt,
+                                                 int skip) {
     const int o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
     const float v[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-    for (int q = 0; q < cnt; ++q) myphi[o[q]] += v[q];
+    for (int q = 0; q < cnt; ++q)
+        if (o[q] != skip) myphi[o[q]] += v[q];
 }
 
-// phi[o[q]] += val[q] for the first cnt positions of one flush batch.  fast: the batch
-// repeats no real feature, so all reads may precede all writes.
+// phi[o[q]] += val[q] for the first cnt positions of one flush batch, except positions
+// whose offset is `skip` (the scratch row of pass-through nodes and padding: a third of
+// the positions of a typical depth-6 tree; the test is uniform across the warp, so a
+// skipped position issues no shared-memory access).  fast: the batch repeats no real
+// feature, so all reads may precede all writes.
 __device__ __forceinline__ void flush_batch(float *myphi, const int (&o)[8], const float (&val)[8], int cnt,
-                                            bool fast) {
+                                            bool fast, int skip) {
     if (fast) {
         float a[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-            if (q < cnt) a[q] = myphi[o[q]];
+            if (q < cnt && o[q] != skip) a[q] = myphi[o[q]];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-            if (q < cnt) myphi[o[q]] = a[q] + val[q];
+            if (q < cnt && o[q] != skip) myphi[o[q]] = a[q] + val[q];
     } else {
         flush_serial(myphi, make_int4(o[0], o[1], o[2], o[3]), make_int4(o[4], o[5], o[6], o[7]),
-                     make_float4(val[0], val[1], val[2], val[3]), make_float4(val[4], val[5], val[6], val[7]), cnt);
+                     make_float4(val[0], val[1], val[2], val[3]), make_float4(val[4], val[5], val[6], val[7]), cnt,
+                     skip);
     }
 }
 
@@ -176,8 +184,8 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
     }
     for (int i = tid; i < (F + 1) * XS; i += TC) sp[i] = 0.0f;
     float *myphi = sp + tid;
+    const int skip = F * XS;  // phi offset of the scratch row
     const CodeReader xr(sx + (size_t)warp * 32 * xb, lane, cb);
-    const float4 *z4 = reinterpret_cast<const float4 *>(job.zero);
     for (int tc0 = 0; tc0 < T; tc0 += X::TCH) {
         const int tcn = min(X::TCH, T - tc0);
         __syncthreads();
@@ -212,13 +220,15 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
                 float4 v[GS][Q];
 #pragma unroll
                 for (int j = 0; j < GS; ++j) {
-                    const bool lj = (lv >> (s0 + j)) & 1ull;
-                    const float4 *src = lj ? tf + ((size_t)(s0 + j) * S::E + ent[s0 + j]) * Q : z4;
+                    const uint32_t lj = (uint32_t)(lv >> (s0 + j)) & 1u;
+                    const float4 *src = tf + ((size_t)(s0 + j) * S::E + ent[s0 + j]) * Q;
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) v[j][k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     if (Q == 2) {
-                        ldg_f8(src, v[j][0], v[j][Q > 1 ? 1 : 0]);
+                        ldg_f8_if(src, v[j][0], v[j][Q > 1 ? 1 : 0], lj);
                     } else {
 #pragma unroll
-                        for (int k = 0; k < Q; ++k) v[j][k] = ldg_f4(src + k);
+                        for (int k = 0; k < Q; ++k) ldg_f4_if(src + k, v[j][k], lj);
                     }
                 }
 #pragma unroll
@@ -244,7 +254,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
                         const int i = i0 + q;
                         val[q] = i < 3 * GS ? reinterpret_cast<const float *>(&v[i / 3][0])[D - 2 + i % 3] : 0.0f;
                     }
-                    flush_batch(myphi, o, val, min(8, 3 * GS - i0), (fok >> (fb >> 3)) & 1u);
+                    flush_batch(myphi, o, val, min(8, 3 * GS - i0), (fok >> (fb >> 3)) & 1u, skip);
                     if (i0 + 8 < 3 * GS) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q) o[q] = on[q];
@@ -262,7 +272,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
                     float val[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) val[q] = u0 + q < S::NS - 1 ? acc[u0 + q] : 0.0f;
-                    flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u);
+                    flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u, skip);
                     if (u0 + 8 < S::NS - 1) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q) o[q] = on[q];

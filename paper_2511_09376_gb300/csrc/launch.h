@@ -26,7 +26,6 @@ struct TreeArrays {
 struct ExplainJob {
     TreeArrays ta;
     const float *sfold;  // folded slot vectors [T][NS][2^(D+1)][SP]
-    const float *zero;   // 64 zero bytes
     int T, F;
 };
 

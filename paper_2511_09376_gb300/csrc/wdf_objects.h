@@ -32,7 +32,6 @@ struct wdf_ensemble {
     wdf::TreeMeta *d_meta = nullptr;
     wdf::CodeCol *d_cols = nullptr;
     float *d_col_thr = nullptr;
-    float *d_zero = nullptr;  // 64 zero bytes: the entry a dead bottom subtree reads
     // tensor-core contraction: K-major tables, 128-row tiles, wait-expiry flag
     float *d_t32t = nullptr;
     int4 *d_tiles128 = nullptr;
@@ -41,7 +40,7 @@ struct wdf_ensemble {
     wdf::TreeArrays arrays() const {
         return wdf::TreeArrays{d_nodes, d_rec, d_meta, d_cols, d_col_thr, (int)pk.cols.size(), pk.code_bytes};
     }
-    wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, d_zero, pk.T, pk.F}; }
+    wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, pk.T, pk.F}; }
     // background state (set_background)
     int has_bg = 0;
     int64_t m = 0;
