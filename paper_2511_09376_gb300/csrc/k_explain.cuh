@@ -13,7 +13,7 @@
 // phi[feature of the node] in the fixed flush order of tree_layout.h, eight at a time:
 // a batch that repeats no feature reads its eight phi values before writing any, so
 // the shared-memory round trips overlap; any other batch adds one by one.  Pass-through
-// nodes map to a scratch row and are skipped.  The order of every floating-point addition into a
+// nodes add into a scratch row.  The order of every floating-point addition into a
 // row's phi depends only on the ensemble, never on which rows share a block.
 //
 // The kernels are templates of the depth; every depth is instantiated in its own
@@ -77,33 +77,29 @@ __device__ __forceinline__ void ldg_f8_if(const float4 *p, float4 &a, float4 &b,
 
 // phi[o[q]] += val[q], q < cnt, one after another: the rare batch that repeats a
 // feature.  Kept out of line so the per-tree loop stays small in the instruction cache.
-static __device__ __noinline__ void flush_serial(float *myphi, int4 oa, int4 ob, float4 va, float4 vb, int cnt,
-                                                 int skip) {
+static __device__ __noinline__ void flush_serial(float *myphi, int4 oa, int4 ob, float4 va, float4 vb, int cnt) {
     const int o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
     const float v[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-    for (int q = 0; q < cnt; ++q)
-        if (o[q] != skip) myphi[o[q]] += v[q];
+    for (int q = 0; q < cnt; ++q) myphi[o[q]] += v[q];
 }
 
-// phi[o[q]] += val[q] for the first cnt positions of one flush batch, except positions
-// whose offset is `skip` (the scratch row of pass-through nodes and padding: a third of
-// the positions of a typical depth-6 tree; the test is uniform across the warp, so a
-// skipped position issues no shared-memory access).  fast: the batch repeats no real
-// feature, so all reads may precede all writes.
+// phi[o[q]] += val[q] for the first cnt positions of one flush batch.  fast: the batch
+// repeats no real feature, so all reads may precede all writes.  Pass-through positions
+// (the scratch row) are not skipped: a predicated-off shared access still takes an L1
+// data-pipe wavefront (ncu), so a test per position only added instructions.
 __device__ __forceinline__ void flush_batch(float *myphi, const int (&o)[8], const float (&val)[8], int cnt,
-                                            bool fast, int skip) {
+                                            bool fast) {
     if (fast) {
         float a[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-            if (q < cnt && o[q] != skip) a[q] = myphi[o[q]];
+            if (q < cnt) a[q] = myphi[o[q]];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-            if (q < cnt && o[q] != skip) myphi[o[q]] = a[q] + val[q];
+            if (q < cnt) myphi[o[q]] = a[q] + val[q];
     } else {
         flush_serial(myphi, make_int4(o[0], o[1], o[2], o[3]), make_int4(o[4], o[5], o[6], o[7]),
-                     make_float4(val[0], val[1], val[2], val[3]), make_float4(val[4], val[5], val[6], val[7]), cnt,
-                     skip);
+                     make_float4(val[0], val[1], val[2], val[3]), make_float4(val[4], val[5], val[6], val[7]), cnt);
     }
 }
 
@@ -184,7 +180,6 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
     }
     for (int i = tid; i < (F + 1) * XS; i += TC) sp[i] = 0.0f;
     float *myphi = sp + tid;
-    const int skip = F * XS;  // phi offset of the scratch row
     const CodeReader xr(sx + (size_t)warp * 32 * xb, lane, cb);
     for (int tc0 = 0; tc0 < T; tc0 += X::TCH) {
         const int tcn = min(X::TCH, T - tc0);
@@ -254,7 +249,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
                         const int i = i0 + q;
                         val[q] = i < 3 * GS ? reinterpret_cast<const float *>(&v[i / 3][0])[D - 2 + i % 3] : 0.0f;
                     }
-                    flush_batch(myphi, o, val, min(8, 3 * GS - i0), (fok >> (fb >> 3)) & 1u, skip);
+                    flush_batch(myphi, o, val, min(8, 3 * GS - i0), (fok >> (fb >> 3)) & 1u);
                     if (i0 + 8 < 3 * GS) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q) o[q] = on[q];
@@ -272,7 +267,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
                     float val[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) val[q] = u0 + q < S::NS - 1 ? acc[u0 + q] : 0.0f;
-                    flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u, skip);
+                    flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u);
                     if (u0 + 8 < S::NS - 1) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q) o[q] = on[q];
