@@ -117,9 +117,9 @@ EXPLAIN_SOURCES = ["k_explain.cuh", "k_explain.cu", "k_codes.cu", "wdf_device.cu
 BACKGROUND_SOURCES = ["k_background.cu", "k_codes.cu", "wdf_device.cuh", "tree_layout.h"]
 
 
-def profiled_traffic(summary: str, sources: list, units: int):
-    """DRAM bytes per launch from a committed ncu summary (per-unit figure x units), or
-    None when the kernel sources changed since the counters were taken."""
+def profiled_fields(summary: str, sources: list):
+    """The key: value lines of a committed ncu summary, or None when the kernel sources
+    changed since its counters were taken (a hash in the summary)."""
     import hashlib
     try:
         text = open(os.path.join(ROOT, "profiles", summary)).read()
@@ -132,7 +132,21 @@ def profiled_traffic(summary: str, sources: list, units: int):
             h.update(f.read())
     if fields.get("source_sha256_16", "").strip() != h.hexdigest()[:16]:
         return None
-    return float(fields["traffic_bytes_per_unit"]) * units
+    return fields
+
+
+def profiled_traffic(summary: str, sources: list, units: int):
+    """DRAM bytes per launch from a committed ncu summary (per-unit figure x units), or
+    None when the kernel sources changed since the counters were taken."""
+    fields = profiled_fields(summary, sources)
+    return None if fields is None else float(fields["traffic_bytes_per_unit"]) * units
+
+
+def profiled_limiter(summary: str, sources: list):
+    """What ncu showed to bound the kernel (e.g. the L1 data pipe's share of its peak
+    wavefront rate), or None when the counters are stale or absent."""
+    fields = profiled_fields(summary, sources)
+    return None if fields is None else fields.get("limiter", "").strip() or None
 
 
 def algorithmic_ops(ens) -> dict:
@@ -295,6 +309,7 @@ def run_ours(args, rank, world, local_rank):
             "unit": "Top/s",
             "frac": achieved / alu_peak_max,
             "traffic": profiled_traffic("k_explain_large.md", EXPLAIN_SOURCES, n),
+            "limiter_ncu": profiled_limiter("k_explain_large.md", EXPLAIN_SOURCES),
             "algorithmic_bytes": hbm_bytes,
             "ops_per_row": ops,
             "peak_basis": f"{sms} SMs x 128 lanes/clk x {peaks.get('sm_max_mhz', 2070.0)} MHz (max SM clock, {peak_kind})",
@@ -310,6 +325,7 @@ def run_ours(args, rank, world, local_rank):
             "unit": "Top/s",
             "frac": bg_ops * m / (background_ms * 1e-3) / 1e12 / alu_peak_max,
             "traffic": profiled_traffic("k_bg_hist_large.md", BACKGROUND_SOURCES, m),
+            "limiter_ncu": profiled_limiter("k_bg_hist_large.md", BACKGROUND_SOURCES),
             "ops_per_row": {"compares": ops["compares"], "leaf_counts": info["n_live_leaves"], "ops": bg_ops},
             "hbm_gbs": B.nbytes / (background_ms * 1e-3) / 1e9,
         },
