@@ -172,9 +172,33 @@ cudaError_t launch_iv_fold(int D, const float *S2, const int32_t *leaf_row, int 
 
 constexpr int kIvThreads = 256;
 
-// Index of (lo, hi), lo < hi, in the row-major upper triangle of an F x F matrix.
-__device__ __forceinline__ int64_t iv_tri(int lo, int hi, int F) {
-    return (int64_t)lo * F - (int64_t)lo * (lo + 1) / 2 + (hi - lo - 1);
+// Index of (lo, hi), lo < hi, in the row-major upper triangle of an F x F matrix (the
+// triangle is in shared memory, so it fits 32-bit arithmetic).
+__device__ __forceinline__ int iv_tri(int lo, int hi, int F) {
+    return lo * F - ((lo * (lo + 1)) >> 1) + (hi - lo - 1);
+}
+
+// Writes one row's full symmetric F x F matrix with a zero diagonal: from the upper
+// triangle in shared memory (SMEM), or by mirroring the upper half accumulated in place.
+// Thread tid takes elements tid, tid + kIvThreads, ...; their (i, j) advance without a
+// division (the step is di rows and dj columns, with at most one carry).
+template <bool SMEM>
+__device__ __forceinline__ void iv_write_row(float *orow, const float *acc, int F, int tid) {
+    const int64_t FF = (int64_t)F * F;
+    int i = tid / F, j = tid - i * F;
+    const int di = kIvThreads / F, dj = kIvThreads - di * F;
+    for (int64_t k = tid; k < FF; k += kIvThreads) {
+        if (SMEM)
+            orow[k] = i == j ? 0.0f : acc[iv_tri(min(i, j), max(i, j), F)];
+        else if (i > j)
+            orow[k] = orow[(size_t)j * F + i];
+        i += di;
+        j += dj;
+        if (j >= F) {
+            j -= F;
+            ++i;
+        }
+    }
 }
 
 __host__ __device__ __forceinline__ size_t iv_up16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -274,14 +298,7 @@ __global__ void __launch_bounds__(kIvThreads) k_explain_iv(const float *__restri
                 }
         }
         __syncthreads();
-        // the full symmetric matrix, zero diagonal
-        for (int64_t k = tid; k < (int64_t)F * F; k += kIvThreads) {
-            const int i = (int)(k / F), j = (int)(k - (int64_t)i * F);
-            if (SMEM)
-                orow[k] = i == j ? 0.0f : acc[iv_tri(min(i, j), max(i, j), F)];
-            else if (i > j)
-                orow[k] = orow[(size_t)j * F + i];
-        }
+        iv_write_row<SMEM>(orow, acc, F, tid);
         __syncthreads();
     }
 }
@@ -405,13 +422,7 @@ __global__ void __launch_bounds__(kIvThreads) k_explain_iv_fold(const float *__r
             }
         }
         __syncthreads();
-        for (int64_t k = tid; k < (int64_t)F * F; k += kIvThreads) {
-            const int i = (int)(k / F), j = (int)(k - (int64_t)i * F);
-            if (SMEM)
-                orow[k] = i == j ? 0.0f : acc[iv_tri(min(i, j), max(i, j), F)];
-            else if (i > j)
-                orow[k] = orow[(size_t)j * F + i];
-        }
+        iv_write_row<SMEM>(orow, acc, F, tid);
         __syncthreads();
     }
 }
