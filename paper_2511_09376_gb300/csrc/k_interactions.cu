@@ -160,7 +160,18 @@ __global__ void k_iv_fold(int D, const float *__restrict__ S2, const int32_t *__
     for (int k = 0; k < FPP; ++k) dst[k] = out[k];
 }
 
-size_t iv_fold_floats(int D, int T) { return D <= 6 ? ((size_t)T << (D - 2 + D + 1)) * iv_fpp(D) : 0; }
+// Words of the depth <= 6 interaction scratch: the folded vectors, then a byte per
+// complete-layout node of every tree (its feature, for F <= 255; 64 bytes per tree).
+static size_t iv_fold_only(int D, int T) { return ((size_t)T << (D - 2 + D + 1)) * iv_fpp(D); }
+size_t iv_fold_floats(int D, int T) { return D <= 6 ? iv_fold_only(D, T) + (size_t)T * 16 : 0; }
+
+// ftab[t][h] = the feature of node h of tree t (h < 2^D - 1; 255 past the last node).
+__global__ void k_iv_feature_bytes(int NI, const int2 *__restrict__ nodes, int T, unsigned char *__restrict__ ftab) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)T * 64) return;
+    const int t = (int)(i >> 6), h = (int)(i & 63);
+    ftab[i] = h < NI ? (unsigned char)__ldg(&nodes[(size_t)t * NI + h].x) : (unsigned char)255;
+}
 
 cudaError_t launch_iv_fold(int D, const float *S2, const int32_t *leaf_row, int T, float *fold, cudaStream_t st) {
     if (D > 6) return cudaErrorInvalidValue;
@@ -308,10 +319,13 @@ __global__ void __launch_bounds__(kIvThreads) k_explain_iv(const float *__restri
 // pairs with r or its children go straight into the triangle, while the pairs of two
 // nodes above the bottom subtrees accumulate in registers (one per (node, ancestor))
 // and are added once per tree.
-template <int D, bool SMEM>
+// FB: the node features come from a byte table (F <= 255), loaded as 64 bytes per tree
+// into registers, instead of one scattered load per feature.
+template <int D, bool SMEM, bool FB>
 __global__ void __launch_bounds__(kIvThreads) k_explain_iv_fold(const float *__restrict__ C, int64_t n, int64_t ldc,
                                                               int F, TreeArrays ta, int T,
-                                                              const float *__restrict__ fold, float *__restrict__ out,
+                                                              const float *__restrict__ fold,
+                                                              const uint4 *__restrict__ ftab, float *__restrict__ out,
                                                               int64_t ldo) {
     using S = Shape<D>;
     constexpr int NW = S::NW, NI = S::NI, NS = S::NS, E = S::E;
@@ -370,6 +384,21 @@ __global__ void __launch_bounds__(kIvThreads) k_explain_iv_fold(const float *__r
             subtree_entries<D>(dw, ent);
             const uint64_t lv = __ldg(&ta.meta[t].live);
             const int2 *nd = ta.nodes + (size_t)t * NI;
+            uint32_t fr[FB ? 16 : 1];
+            if constexpr (FB) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 w = __ldg(ftab + (size_t)t * 4 + q);
+                    fr[4 * q] = w.x; fr[4 * q + 1] = w.y; fr[4 * q + 2] = w.z; fr[4 * q + 3] = w.w;
+                }
+            }
+            // feature of node h (h a compile-time constant in every use)
+            auto feat = [&](int h) -> int {
+                if constexpr (FB)
+                    return (int)((fr[h >> 2] >> ((h & 3) * 8)) & 0xFFu);
+                else
+                    return __ldg(&nd[h].x);
+            };
             float up[UP];
 #pragma unroll
             for (int k = 0; k < UP; ++k) up[k] = 0.0f;
@@ -386,10 +415,10 @@ __global__ void __launch_bounds__(kIvThreads) k_explain_iv_fold(const float *__r
                 }
                 int fs[D + 1];  // features of the slots
 #pragma unroll
-                for (int k = 0; k < D - 2; ++k) fs[k] = __ldg(&nd[((r + 1) >> (D - 2 - k)) - 1].x);
-                fs[D - 2] = __ldg(&nd[r].x);
-                fs[D - 1] = __ldg(&nd[2 * r + 1].x);
-                fs[D] = __ldg(&nd[2 * r + 2].x);
+                for (int k = 0; k < D - 2; ++k) fs[k] = feat(((r + 1) >> (D - 2 - k)) - 1);
+                fs[D - 2] = feat(r);
+                fs[D - 1] = feat(2 * r + 1);
+                fs[D] = feat(2 * r + 2);
                 // pairs of two ancestors: into the (node, ancestor) registers
 #pragma unroll
                 for (int kv = 1; kv < D - 2; ++kv) {
@@ -413,11 +442,11 @@ __global__ void __launch_bounds__(kIvThreads) k_explain_iv_fold(const float *__r
 #pragma unroll
             for (int h = 1; h < NS - 1; ++h) {
                 const int dh = 31 - __clz(h + 1);  // depth of node h
-                const int fh = __ldg(&nd[h].x);
+                const int fh = feat(h);
 #pragma unroll
                 for (int ku = 0; ku < dh; ++ku, ++k) {
                     const int anc = ((h + 1) >> (dh - ku)) - 1;
-                    add(__ldg(&nd[anc].x), fh, up[k]);
+                    add(feat(anc), fh, up[k]);
                 }
             }
         }
@@ -435,7 +464,7 @@ size_t iv_smem_bytes(int D, int F, int T, int n_cols, bool smem_acc) {
 
 template <int D, bool SMEM>
 static cudaError_t iv_t(const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
-                        const int32_t *group_leaf, int n_live, const float *S2T, const float *fold, float *out,
+                        const int32_t *group_leaf, int n_live, const float *S2T, float *fold, float *out,
                         int64_t ldo, const DevInfo &dev, cudaStream_t st) {
     const size_t smem = iv_smem_bytes(D, F, T, ta.n_cols, SMEM);
     if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
@@ -445,13 +474,21 @@ static cudaError_t iv_t(const float *C, int64_t n, int64_t ldc, int F, const Tre
     bool done = false;
     if constexpr (D <= 6) {
         if (fold != nullptr) {
-            auto kern = k_explain_iv_fold<D, SMEM>;
+            // node features as bytes when they fit (the table follows the folded vectors)
+            const bool fb = F <= 255;
+            uint4 *ftab = reinterpret_cast<uint4 *>(fold + iv_fold_only(D, T));
+            if (fb) {
+                k_iv_feature_bytes<<<(unsigned)(((int64_t)T * 64 + 255) / 256), 256, 0, st>>>(
+                    Shape<D>::NI, ta.nodes, T, reinterpret_cast<unsigned char *>(ftab));
+                count_launches(1);
+            }
+            auto kern = fb ? k_explain_iv_fold<D, SMEM, true> : k_explain_iv_fold<D, SMEM, false>;
             err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (err == cudaSuccess)
                 err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kIvThreads, smem);
             if (err != cudaSuccess) return err;
             const int64_t grid = std::min<int64_t>(cap, (int64_t)dev.sms * std::max(per_sm, 1));
-            kern<<<(unsigned)grid, kIvThreads, smem, st>>>(C, n, ldc, F, ta, T, fold, out, ldo);
+            kern<<<(unsigned)grid, kIvThreads, smem, st>>>(C, n, ldc, F, ta, T, fold, ftab, out, ldo);
             done = true;
         }
     }
@@ -469,7 +506,7 @@ static cudaError_t iv_t(const float *C, int64_t n, int64_t ldc, int F, const Tre
 
 template <int D>
 static cudaError_t iv_d(const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
-                        const int32_t *group_leaf, int n_live, const float *S2T, const float *fold, float *out,
+                        const int32_t *group_leaf, int n_live, const float *S2T, float *fold, float *out,
                         int64_t ldo, const DevInfo &dev, cudaStream_t st) {
     // the triangle in shared memory while two blocks still fit per SM, else in place
     if (iv_smem_bytes(D, F, T, ta.n_cols, true) <= dev.smem_optin / 2)
@@ -478,7 +515,7 @@ static cudaError_t iv_d(const float *C, int64_t n, int64_t ldc, int F, const Tre
 }
 
 cudaError_t launch_explain_iv(int D, const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
-                              const int32_t *group_leaf, int n_live, const float *S2T, const float *fold, float *out,
+                              const int32_t *group_leaf, int n_live, const float *S2T, float *fold, float *out,
                               int64_t ldo, const DevInfo &dev, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     switch (D) {

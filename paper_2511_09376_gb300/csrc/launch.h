@@ -120,12 +120,13 @@ cudaError_t launch_explain_batch(int D, const ExplainJob *jobs, const BatchReque
 // out [n][F][F] at row stride ldo.
 cudaError_t launch_tables_iv(int D, int metric, const uint32_t *sig_keys, int G, float *t2, cudaStream_t st);
 cudaError_t launch_iv_pack(int D, int PP, const float *S2, int n_live, float *S2T, cudaStream_t st);
-// depth <= 6: the pair values folded per (tree, bottom subtree, entry), iv_fold_floats
-// floats; the consumer kernel then takes whole trees (fold non-null) instead of leaves
+// depth <= 6: the pair values folded per (tree, bottom subtree, entry), followed by a
+// byte table of node features (iv_fold_floats words in all; launch_explain_iv writes the
+// table); the consumer kernel then takes whole trees (fold non-null) instead of leaves
 size_t iv_fold_floats(int D, int T);
 cudaError_t launch_iv_fold(int D, const float *S2, const int32_t *leaf_row, int T, float *fold, cudaStream_t st);
 cudaError_t launch_explain_iv(int D, const float *C, int64_t n, int64_t ldc, int F, const TreeArrays &ta, int T,
-                              const int32_t *group_leaf, int n_live, const float *S2T, const float *fold, float *out,
+                              const int32_t *group_leaf, int n_live, const float *S2T, float *fold, float *out,
                               int64_t ldo, const DevInfo &dev, cudaStream_t st);
 
 // FP64 column means of |phi| and phi: partial sums per row block, then a fixed-order
