@@ -161,9 +161,36 @@ __global__ void k_iv_fold(int D, const float *__restrict__ S2, const int32_t *__
 }
 
 // Words of the depth <= 6 interaction scratch: the folded vectors, then a byte per
-// complete-layout node of every tree (its feature, for F <= 255; 64 bytes per tree).
+// complete-layout node of every tree (its feature; 16 words per tree), then every tree's
+// decision records packed into words (kIvPackWords per tree); the last two are used when
+// F <= 255 and the codes take one byte.
+constexpr int kIvPackWords = 68;
 static size_t iv_fold_only(int D, int T) { return ((size_t)T << (D - 2 + D + 1)) * iv_fpp(D); }
-size_t iv_fold_floats(int D, int T) { return D <= 6 ? iv_fold_only(D, T) + (size_t)T * 16 : 0; }
+size_t iv_fold_floats(int D, int T) { return D <= 6 ? iv_fold_only(D, T) + (size_t)T * (16 + kIvPackWords) : 0; }
+
+// prec[t]: words 0-2 = the tree's pass-through decision words and its real inner-node
+// count, then one word per real node: column << 16 | (rank + 1) << 7 | decision bit (the
+// row goes left at the node when its code < rank + 1).  One-byte codes only.
+__global__ void k_iv_pack_records(int NW, int NI, const int4 *__restrict__ rec, const TreeMeta *__restrict__ meta,
+                                  int T, uint32_t *__restrict__ prec) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)T * kIvPackWords) return;
+    const int t = (int)(i / kIvPackWords), k = (int)(i % kIvPackWords);
+    const int cnt = meta[t].wend[NW - 1];
+    uint32_t w = 0u;
+    if (k == 0) {
+        w = meta[t].pt[0];
+    } else if (k == 1) {
+        w = NW == 2 ? meta[t].pt[1] : 0u;
+    } else if (k == 2) {
+        w = (uint32_t)cnt;
+    } else if (k >= 4 && k - 4 < cnt) {
+        const int4 r = rec[(size_t)t * NI + (k - 4)];
+        const int bit = r.z ? __ffs(r.z) - 1 : 32 + __ffs(r.w) - 1;
+        w = ((uint32_t)(r.x >> 5) << 16) | ((uint32_t)(r.y + 1) << 7) | (uint32_t)bit;
+    }
+    prec[i] = w;
+}
 
 // ftab[t][h] = the feature of node h of tree t (h < 2^D - 1; 255 past the last node).
 __global__ void k_iv_feature_bytes(int NI, const int2 *__restrict__ nodes, int T, unsigned char *__restrict__ ftab) {
@@ -319,13 +346,15 @@ __global__ void __launch_bounds__(kIvThreads) k_explain_iv(const float *__restri
 // pairs with r or its children go straight into the triangle, while the pairs of two
 // nodes above the bottom subtrees accumulate in registers (one per (node, ancestor))
 // and are added once per tree.
-// FB: the node features come from a byte table (F <= 255), loaded as 64 bytes per tree
-// into registers, instead of one scattered load per feature.
+// FB (F <= 255, one-byte codes): the node features come from a byte table, loaded as
+// 64 bytes per tree into registers, instead of one scattered load per feature, and the
+// decision records from the packed table (four nodes per 16-byte load).
 template <int D, bool SMEM, bool FB>
 __global__ void __launch_bounds__(kIvThreads) k_explain_iv_fold(const float *__restrict__ C, int64_t n, int64_t ldc,
                                                               int F, TreeArrays ta, int T,
                                                               const float *__restrict__ fold,
-                                                              const uint4 *__restrict__ ftab, float *__restrict__ out,
+                                                              const uint4 *__restrict__ ftab,
+                                                              const uint4 *__restrict__ prec, float *__restrict__ out,
                                                               int64_t ldo) {
     using S = Shape<D>;
     constexpr int NW = S::NW, NI = S::NI, NS = S::NS, E = S::E;
@@ -354,17 +383,34 @@ __global__ void __launch_bounds__(kIvThreads) k_explain_iv_fold(const float *__r
         }
         __syncthreads();
         for (int t = tid; t < T; t += kIvThreads) {
-            const TreeMeta m = load_meta(ta.meta + t);
-            const int4 *rec = reinterpret_cast<const int4 *>(ta.rec) + (size_t)t * NI;
-            uint32_t lo = 0u, hi = 0u;
-            for (int i = 0; i < m.wend[NW - 1]; ++i) {
-                const int4 r = __ldg(rec + i);
-                const uint32_t s = 0u - (uint32_t)(scode[r.x >> cshift] <= r.y);
-                lo |= (uint32_t)r.z & s;
-                hi |= (uint32_t)r.w & s;
+            if constexpr (FB) {
+                const uint4 *pr = prec + (size_t)t * (kIvPackWords / 4);
+                const uint4 hd = __ldg(pr);
+                uint64_t d = (uint64_t)hd.x | ((uint64_t)hd.y << 32);
+                const int cnt = (int)hd.z;
+                for (int i0 = 0; i0 < cnt; i0 += 4) {
+                    const uint4 w4 = __ldg(pr + 1 + (i0 >> 2));
+                    const uint32_t a[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (i0 + c < cnt)
+                            d |= (uint64_t)(scode[a[c] >> 16] < (int)((a[c] >> 7) & 511u)) << (a[c] & 127u);
+                }
+                sdw[t * NW] = (uint32_t)d;
+                if (NW == 2) sdw[t * NW + 1] = (uint32_t)(d >> 32);
+            } else {
+                const TreeMeta m = load_meta(ta.meta + t);
+                const int4 *rec = reinterpret_cast<const int4 *>(ta.rec) + (size_t)t * NI;
+                uint32_t lo = 0u, hi = 0u;
+                for (int i = 0; i < m.wend[NW - 1]; ++i) {
+                    const int4 r = __ldg(rec + i);
+                    const uint32_t s = 0u - (uint32_t)(scode[r.x >> cshift] <= r.y);
+                    lo |= (uint32_t)r.z & s;
+                    hi |= (uint32_t)r.w & s;
+                }
+                sdw[t * NW] = m.pt[0] | lo;
+                if (NW == 2) sdw[t * NW + 1] = m.pt[1] | hi;
             }
-            sdw[t * NW] = m.pt[0] | lo;
-            if (NW == 2) sdw[t * NW + 1] = m.pt[1] | hi;
         }
         __syncthreads();
         auto add = [&](int fa, int fb, float v) {
@@ -474,13 +520,18 @@ static cudaError_t iv_t(const float *C, int64_t n, int64_t ldc, int F, const Tre
     bool done = false;
     if constexpr (D <= 6) {
         if (fold != nullptr) {
-            // node features as bytes when they fit (the table follows the folded vectors)
-            const bool fb = F <= 255;
+            // node features as bytes and packed decision records when they fit (the tables
+            // follow the folded vectors)
+            const bool fb = F <= 255 && ta.code_bytes == 1;
             uint4 *ftab = reinterpret_cast<uint4 *>(fold + iv_fold_only(D, T));
+            uint4 *prec = ftab + (size_t)T * 4;
             if (fb) {
                 k_iv_feature_bytes<<<(unsigned)(((int64_t)T * 64 + 255) / 256), 256, 0, st>>>(
                     Shape<D>::NI, ta.nodes, T, reinterpret_cast<unsigned char *>(ftab));
-                count_launches(1);
+                k_iv_pack_records<<<(unsigned)(((int64_t)T * kIvPackWords + 255) / 256), 256, 0, st>>>(
+                    Shape<D>::NW, Shape<D>::NI, reinterpret_cast<const int4 *>(ta.rec), ta.meta, T,
+                    reinterpret_cast<uint32_t *>(prec));
+                count_launches(2);
             }
             auto kern = fb ? k_explain_iv_fold<D, SMEM, true> : k_explain_iv_fold<D, SMEM, false>;
             err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -488,7 +539,7 @@ static cudaError_t iv_t(const float *C, int64_t n, int64_t ldc, int F, const Tre
                 err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kIvThreads, smem);
             if (err != cudaSuccess) return err;
             const int64_t grid = std::min<int64_t>(cap, (int64_t)dev.sms * std::max(per_sm, 1));
-            kern<<<(unsigned)grid, kIvThreads, smem, st>>>(C, n, ldc, F, ta, T, fold, ftab, out, ldo);
+            kern<<<(unsigned)grid, kIvThreads, smem, st>>>(C, n, ldc, F, ta, T, fold, ftab, prec, out, ldo);
             done = true;
         }
     }
