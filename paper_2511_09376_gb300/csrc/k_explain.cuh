@@ -203,7 +203,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
             uint32_t ent[S::NS];
             subtree_entries<D>(dw, ent);
             const uint64_t lv = mt.live;
-            const uint32_t fok = mt.flush;
+            const uint32_t fok = mt.flush, real = mt.real;
             const float4 *tf = reinterpret_cast<const float4 *>(sfold + (size_t)t * S::NS * S::E * S::SP);
             float acc[NA];
 #pragma unroll
@@ -249,7 +249,8 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
                         const int i = i0 + q;
                         val[q] = i < 3 * GS ? reinterpret_cast<const float *>(&v[i / 3][0])[D - 2 + i % 3] : 0.0f;
                     }
-                    flush_batch(myphi, o, val, min(8, 3 * GS - i0), (fok >> (fb >> 3)) & 1u);
+                    if ((real >> (fb >> 3)) & 1u)  // a batch of pass-through nodes only adds nothing
+                        flush_batch(myphi, o, val, min(8, 3 * GS - i0), (fok >> (fb >> 3)) & 1u);
                     if (i0 + 8 < 3 * GS) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q) o[q] = on[q];
@@ -267,7 +268,8 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
                     float val[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) val[q] = u0 + q < S::NS - 1 ? acc[u0 + q] : 0.0f;
-                    flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u);
+                    if ((real >> ((FLB + u0) >> 3)) & 1u)
+                        flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u);
                     if (u0 + 8 < S::NS - 1) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q) o[q] = on[q];

@@ -144,6 +144,10 @@ void build_records(Packed *pp) {
                     ok = fi == F || fi != fj;  // pass-through nodes all write the scratch row
                 }
             if (ok) m.flush |= 1u << b;
+            for (int i = 8 * b; i < 8 * b + 8; ++i) {
+                const int v = flush_node(D, i);
+                if (v >= 0 && p.node_feat[(size_t)t * NI + v] != F) m.real |= 1u << b;
+            }
         }
     }
 }

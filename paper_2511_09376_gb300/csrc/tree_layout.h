@@ -43,7 +43,7 @@ struct TreeMeta {
     uint64_t live;    // bit s: bottom subtree s has a non-zero leaf
     uint32_t flush;   // bit b: consumer flush batch b repeats no real feature
     uint8_t wend[8];  // NodeRec index one past the last node of word w
-    uint32_t pad;
+    uint32_t real;    // bit b: consumer flush batch b holds a real (not pass-through) node
 };
 static_assert(sizeof(NodeRec) == 16, "NodeRec is one 16-byte load");
 static_assert(sizeof(TreeMeta) == 56, "TreeMeta layout");
