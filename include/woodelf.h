@@ -234,17 +234,20 @@ wdf_status wdf_batch_tile_rows(const wdf_batch *batch, int32_t depth, int32_t *t
 
 /*
  * Continuous-batching server (project addition).  Requests in host memory queue in
- * FIFO order; a scheduler thread admits them while one of n_slots execution slots is
- * free and their device buffers (2 * n * F * 4 bytes) fit in device_budget_bytes, and
- * runs each admitted wave (up to max_wave_requests requests) as copies in, ONE batch
- * launch (wdf_batch_explain) and copies out on the slot's stream.  Waves of different
- * slots overlap on the GPU.  Every ensemble must have its background set and must
- * outlive the server.  A request's phi equals what wdf_explain gives for the same rows,
- * whatever shares its wave.
+ * arrival order and are served in parts of at most 8192 rows.  Whenever one of n_slots
+ * execution slots is free, a scheduler thread fills a wave by taking one part from each
+ * queued request in turn (round robin, so a large request does not hold back the ones
+ * behind it) until the wave has max_wave_requests parts, about 16M rows x trees of
+ * work, or the next part's device buffers (2 * rows * F * 4 bytes) would exceed
+ * device_budget_bytes; it runs the wave as copies in, ONE batch launch
+ * (wdf_batch_explain) and copies out on the slot's stream.  Waves of different slots
+ * overlap on the GPU.  A request completes with its last part.  Every ensemble must have
+ * its background set and must outlive the server.  A request's phi equals what
+ * wdf_explain gives for the same rows, whatever shares its waves.
  * wdf_server_submit: C (n x F, row stride ldc) is read and phi (row stride ldphi)
  * written asynchronously: both must stay valid until wdf_server_wait / _poll reports the
- * ticket done.  WDF_ENOMEM if the request alone exceeds the budget, WDF_EBUSY while
- * shutting down.  wdf_server_wait: WDF_ETIMEOUT if not done within timeout_ms.
+ * ticket done.  WDF_ENOMEM if one part of the request (min(n, 8192) rows) alone exceeds
+ * the budget, WDF_EBUSY while shutting down.  wdf_server_wait: WDF_ETIMEOUT if not done within timeout_ms.
  * wdf_server_stats: latency percentiles are over requests completed since creation or
  * the last wdf_server_reset_stats, measured from submit to completion; rows_per_s over
  * the span from the first submit to the last completion.  wdf_server_destroy finishes

@@ -1,15 +1,19 @@
 // Continuous-batching request server over device-resident ensembles.
 //
-// Requests (host buffers) queue in FIFO order.  A scheduler thread admits queued
-// requests while an execution slot is free and their device buffers (consumer rows and
-// phi) fit in the remaining device-memory budget; the admitted requests form one wave:
-// host-to-device copies, ONE batch-graph launch for all of them (wdf_batch_explain, each
-// slot owns its own batch object), device-to-host copies of phi, then an event.  Waves
-// of different slots run concurrently on their own streams, so requests that arrive
-// while others are on the GPU start as soon as a slot and memory free up.  Completion is
-// detected by polling the slot events; latency is measured from submit to completion.
-// A request's rows are computed by exactly the same per-row code whatever else shares
-// its wave, so its phi does not depend on the mix.
+// Requests (host buffers) queue in arrival order and are served in parts of at most
+// kPartRows rows.  A scheduler thread fills a wave whenever an execution slot is free:
+// it walks the queue taking one part from each request in turn (round robin), so a
+// large request cannot hold back the requests behind it, until the wave has
+// max_wave parts or kWaveWork row-trees of work or the next part's device buffers
+// (consumer rows and phi) would exceed the remaining device-memory budget.  A wave is
+// host-to-device copies, ONE batch-graph launch for all its parts (wdf_batch_explain,
+// each slot owns its own batch object), device-to-host copies of phi, then an event.
+// Waves of different slots run concurrently on their own streams, so requests that
+// arrive while others are on the GPU start as soon as a slot and memory free up.
+// Completion is detected by polling the slot events; a request completes when its last
+// part does, and its latency is measured from submit to then.  Every row is computed by
+// exactly the same per-row code whatever else shares its wave, so a request's phi does
+// not depend on the mix or on how it was cut into parts.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -32,6 +36,9 @@ wdf_status fail(wdf_status s, const std::string &msg) {
     return s;
 }
 
+constexpr int64_t kPartRows = 8192;         // rows per part of a request
+constexpr int64_t kWaveWork = 16ll << 20;    // row-trees per wave (rows x trees of the ensemble)
+
 struct Request {
     uint64_t ticket = 0;
     int ens = 0;
@@ -39,13 +46,26 @@ struct Request {
     float *phi = nullptr;
     int64_t n = 0, ldc = 0, ldp = 0;
     int F = 0;
-    int64_t bytes = 0;  // device bytes while in flight
     Clock::time_point t_submit;
+    int64_t next = 0;      // first row not yet in a wave
+    int64_t finished = 0;  // rows whose wave has completed
+    bool failed = false;
+};
+
+// Rows [r0, r0 + n) of one request.
+struct Part {
+    uint64_t ticket = 0;
+    int ens = 0;
+    const float *C = nullptr;
+    float *phi = nullptr;
+    int64_t n = 0, ldc = 0, ldp = 0;
+    int F = 0;
+    int64_t bytes = 0;  // device bytes while in flight
     float *d_C = nullptr, *d_phi = nullptr;
 };
 
 struct Wave {
-    std::vector<Request> reqs;
+    std::vector<Part> parts;
     int slot = -1;
     int64_t bytes = 0;
 };
@@ -64,8 +84,9 @@ struct wdf_server {
     std::vector<Wave> wave;          // per slot, empty when free
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request> pending;
-    std::map<uint64_t, int> state;  // 0 queued, 1 in flight, 2 done, 3 failed
+    std::map<uint64_t, Request> active;  // submitted and not yet complete
+    std::deque<uint64_t> pending;        // tickets with rows not yet in a wave, in arrival order
+    std::map<uint64_t, int> state;       // 0 queued, 1 in flight, 2 done, 3 failed
     uint64_t next_ticket = 1;
     int64_t in_use = 0;
     bool stop = false;
@@ -87,7 +108,7 @@ cudaError_t launch_wave(wdf_server *s, Wave &w) {
     std::vector<const float *> C;
     std::vector<float *> phi;
     std::vector<int64_t> n, ldc, ldp;
-    for (Request &r : w.reqs) {
+    for (Part &r : w.parts) {
         const size_t row_bytes = (size_t)r.F * sizeof(float);
         cudaError_t e = cudaMallocAsync((void **)&r.d_C, r.n * row_bytes, st);
         if (e == cudaSuccess) e = cudaMallocAsync((void **)&r.d_phi, r.n * row_bytes, st);
@@ -109,7 +130,7 @@ cudaError_t launch_wave(wdf_server *s, Wave &w) {
         s->error = wdf_last_error();
         return cudaErrorUnknown;
     }
-    for (Request &r : w.reqs) {
+    for (Part &r : w.parts) {
         const size_t row_bytes = (size_t)r.F * sizeof(float);
         cudaError_t e = cudaMemcpy2DAsync(r.phi, (size_t)r.ldp * sizeof(float), r.d_phi, row_bytes, row_bytes,
                                           (size_t)r.n, cudaMemcpyDeviceToHost, st);
@@ -120,6 +141,63 @@ cudaError_t launch_wave(wdf_server *s, Wave &w) {
     return cudaEventRecord(s->done_ev[(size_t)w.slot], st);
 }
 
+// A part's rows are done (ok or failed): the request completes with its last part.
+void finish_part(wdf_server *s, const Part &p, bool ok, Clock::time_point now) {
+    auto it = s->active.find(p.ticket);
+    if (it == s->active.end()) return;
+    Request &r = it->second;
+    r.finished += p.n;
+    if (!ok) r.failed = true;
+    if (r.finished < r.n) return;
+    s->state[r.ticket] = r.failed ? 3 : 2;
+    s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r.t_submit).count());
+    s->rows_done += r.n;
+    ++s->completed;
+    s->active.erase(it);
+}
+
+// Fill a wave for a free slot from the queue, one part per request per pass.
+Wave fill_wave(wdf_server *s, int slot) {
+    Wave w;
+    w.slot = slot;
+    int64_t work = 0;
+    bool added = true;
+    while (added && (int)w.parts.size() < s->max_wave && work < kWaveWork) {
+        added = false;
+        for (auto it = s->pending.begin();
+             it != s->pending.end() && (int)w.parts.size() < s->max_wave && work < kWaveWork;) {
+            Request &r = s->active[*it];
+            const int64_t rows = std::min(kPartRows, r.n - r.next);
+            const int64_t bytes = 2 * rows * (int64_t)r.F * (int64_t)sizeof(float);
+            if (s->in_use + w.bytes + bytes > s->budget) {
+                ++it;  // does not fit now; a smaller part further back may
+                continue;
+            }
+            Part p;
+            p.ticket = r.ticket;
+            p.ens = r.ens;
+            p.C = r.C + r.next * r.ldc;
+            p.phi = r.phi + r.next * r.ldp;
+            p.n = rows;
+            p.ldc = r.ldc;
+            p.ldp = r.ldp;
+            p.F = r.F;
+            p.bytes = bytes;
+            w.parts.push_back(p);
+            w.bytes += bytes;
+            work += rows * (int64_t)s->ens[(size_t)r.ens]->pk.T;
+            r.next += rows;
+            s->state[r.ticket] = 1;
+            added = true;
+            if (r.next == r.n)
+                it = s->pending.erase(it);
+            else
+                ++it;
+        }
+    }
+    return w;
+}
+
 void run(wdf_server *s) {
     cudaSetDevice(s->ctx->device);
     std::unique_lock<std::mutex> lk(s->mu);
@@ -128,39 +206,26 @@ void run(wdf_server *s) {
         bool any_inflight = false;
         for (int k = 0; k < s->n_slots; ++k) {
             Wave &w = s->wave[(size_t)k];
-            if (w.reqs.empty()) continue;
+            if (w.parts.empty()) continue;
             const cudaError_t q = cudaEventQuery(s->done_ev[(size_t)k]);
             if (q == cudaErrorNotReady) {
                 any_inflight = true;
                 continue;
             }
             const auto now = Clock::now();
-            for (const Request &r : w.reqs) {
-                s->state[r.ticket] = (q == cudaSuccess) ? 2 : 3;
-                s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r.t_submit).count());
-                s->rows_done += r.n;
-                ++s->completed;
-            }
+            for (const Part &p : w.parts) finish_part(s, p, q == cudaSuccess, now);
             if (q != cudaSuccess) s->error = std::string("wave failed: ") + cudaGetErrorString(q);
             s->t_last = now;
             s->in_use -= w.bytes;
             w = Wave();
             s->cv_done.notify_all();
         }
-        // admit queued requests into free slots
+        // fill free slots from the queue
         bool launched = false;
         for (int k = 0; k < s->n_slots && !s->pending.empty(); ++k) {
-            if (!s->wave[(size_t)k].reqs.empty()) continue;
-            Wave w;
-            w.slot = k;
-            while (!s->pending.empty() && (int)w.reqs.size() < s->max_wave &&
-                   s->in_use + w.bytes + s->pending.front().bytes <= s->budget) {
-                w.bytes += s->pending.front().bytes;
-                w.reqs.push_back(s->pending.front());
-                s->state[s->pending.front().ticket] = 1;
-                s->pending.pop_front();
-            }
-            if (w.reqs.empty()) break;  // the head does not fit until memory frees up
+            if (!s->wave[(size_t)k].parts.empty()) continue;
+            Wave w = fill_wave(s, k);
+            if (w.parts.empty()) break;  // no part fits until memory frees up
             s->in_use += w.bytes;
             ++s->waves;
             lk.unlock();
@@ -168,7 +233,8 @@ void run(wdf_server *s) {
             lk.lock();
             if (e != cudaSuccess) {
                 s->error = std::string("launch failed: ") + cudaGetErrorString(e);
-                for (const Request &r : w.reqs) s->state[r.ticket] = 3;
+                const auto now = Clock::now();
+                for (const Part &p : w.parts) finish_part(s, p, false, now);
                 s->in_use -= w.bytes;
                 s->cv_done.notify_all();
                 continue;
@@ -262,8 +328,8 @@ wdf_status wdf_server_submit(wdf_server *s, int32_t ensemble_index, const float 
     r.ldc = ldc;
     r.ldp = ldphi;
     r.F = F;
-    r.bytes = 2 * n * (int64_t)F * (int64_t)sizeof(float);
-    if (r.bytes > s->budget) return fail(WDF_ENOMEM, "request larger than the server's device-memory budget");
+    if (2 * std::min(n, kPartRows) * (int64_t)F * (int64_t)sizeof(float) > s->budget)
+        return fail(WDF_ENOMEM, "a part of the request is larger than the server's device-memory budget");
     r.t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -272,7 +338,8 @@ wdf_status wdf_server_submit(wdf_server *s, int32_t ensemble_index, const float 
         s->state[r.ticket] = 0;
         if (s->submitted == 0) s->t_first = r.t_submit;
         ++s->submitted;
-        s->pending.push_back(r);
+        s->active[r.ticket] = r;
+        s->pending.push_back(r.ticket);
     }
     s->cv_work.notify_one();
     *ticket = r.ticket;
