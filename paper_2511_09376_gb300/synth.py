@@ -21,6 +21,8 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -171,6 +173,15 @@ def make(w: Workload | str, n_consumers: int | None = None, n_background: int | 
     return ens, C, B
 
 
+def consumers(w: Workload | str, n: int) -> np.ndarray:
+    """The first n consumer rows of a workload: the rows make(w, n_consumers=n) returns,
+    without drawing the ensemble or the background."""
+    if isinstance(w, str):
+        w = WORKLOADS[w]
+    _, _, s_cons = np.random.SeedSequence(w.seed).spawn(3)
+    return draw_rows(s_cons, n, w.n_features, w.n_gauss)
+
+
 def node_covers(ens: Ensemble, X: np.ndarray) -> np.ndarray:
     """Cover of every node: how many rows of X reach it (what a trained model records
     for its training rows), indexed like the node arrays, as float64."""
@@ -244,13 +255,20 @@ _CHUNK = 1 << 16
 
 def draw_rows(seed_seq: np.random.SeedSequence, rows: int, n_features: int, n_gauss: int) -> np.ndarray:
     """Rows drawn in fixed chunks of 65,536 from per-chunk child streams, so a prefix
-    of a long draw equals a short draw and long draws can be produced in parallel."""
+    of a long draw equals a short draw and the chunks are drawn in parallel threads
+    (numpy's generators release the GIL while filling arrays)."""
     out = np.empty((rows, n_features), dtype=np.float32)
     n_chunks = max(1, math.ceil(rows / _CHUNK))
     kids = np.random.SeedSequence(seed_seq.entropy, spawn_key=seed_seq.spawn_key).spawn(n_chunks)
-    for i in range(n_chunks):
+
+    def chunk(i):
         lo, hi = i * _CHUNK, min(rows, (i + 1) * _CHUNK)
-        if hi <= lo:
-            break
-        out[lo:hi] = draw_features(np.random.Generator(np.random.PCG64(kids[i])), hi - lo, n_features, n_gauss)
+        if hi > lo:
+            out[lo:hi] = draw_features(np.random.Generator(np.random.PCG64(kids[i])), hi - lo, n_features, n_gauss)
+
+    if n_chunks == 1:
+        chunk(0)
+    else:
+        with ThreadPoolExecutor(max_workers=min(n_chunks, os.cpu_count() or 1, 16)) as ex:
+            list(ex.map(chunk, range(n_chunks)))
     return out

@@ -36,3 +36,21 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+# The FP32-mode bar of every phi comparison against the FP64 oracle:
+# |gpu - oracle| <= 1e-6 + 1e-5 |oracle|, element by element.
+PHI_ATOL, PHI_RTOL = 1e-6, 1e-5
+
+
+def assert_phi_close(got, want, label=""):
+    import numpy as np
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    assert got.shape == want.shape, (label, got.shape, want.shape)
+    err = np.abs(got - want)
+    bound = PHI_ATOL + PHI_RTOL * np.abs(want)
+    bad = err > bound
+    assert not bad.any(), (f"{label}: {int(bad.sum())} of {bad.size} entries off; worst excess "
+                           f"{(err - bound).max():.3e}, max |err| {err.max():.3e}")
+    return float(err.max()) if err.size else 0.0

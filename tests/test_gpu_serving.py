@@ -95,3 +95,48 @@ def test_budget_admission_and_rejection(setup):
     assert ei.value.status == 2
     assert wdf.server_stats(srv)["device_bytes_in_use"] == 0
     srv.close()
+
+
+def test_multi_part_requests_strided_across_waves_and_slots(setup):
+    """Requests longer than one part (8,192 rows) with row strides larger than F on both
+    sides: with two slots and waves of at most two parts, the parts of one request land
+    in different waves and slots; phi still equals the single call bit for bit."""
+    wdf, ctx, ens = setup
+    srv = wdf.server_create(ctx, ens, device_budget_bytes=1 << 30, n_slots=2, max_wave=2)
+    subs = []
+    for j, (k, n) in enumerate([(1, 8193), (0, 20011), (2, 16384), (1, 3)]):
+        F = wdf.ensemble_info(ens[k])["n_features"]
+        Cw = np.full((n, F + 4), np.nan, np.float32)
+        Cw[:, :F] = _rows(k, n, F, 500 + j)
+        phw = np.full((n, F + 6), -3.0, np.float32)
+        t, _ = wdf.server_submit(srv, k, Cw[:, :F], phi=phw[:, :F])
+        subs.append((t, k, Cw, phw, F))
+    for t, *_ in subs:
+        wdf.server_wait(srv, t)
+    for t, k, Cw, phw, F in subs:
+        np.testing.assert_array_equal(phw[:, :F], wdf.explain(ens[k], np.ascontiguousarray(Cw[:, :F])))
+        assert (phw[:, F:] == -3.0).all()
+    st = wdf.server_stats(srv)
+    assert st["completed"] == st["submitted"] == len(subs)
+    assert st["device_bytes_in_use"] == 0 and st["queued"] == 0
+    assert st["waves"] >= 4  # 2 + 3 + 2 + 1 = 8 parts in waves of at most two parts
+    srv.close()
+
+
+def test_small_requests_use_the_express_slot(setup):
+    """With two or more slots, small requests are served while large parts hold the
+    other slots: a single-row request submitted behind many large parts completes
+    before them."""
+    wdf, ctx, ens = setup
+    F = wdf.ensemble_info(ens[1])["n_features"]
+    srv = wdf.server_create(ctx, ens, device_budget_bytes=4 << 30, n_slots=2, max_wave=1)
+    big = [wdf.server_submit(srv, 1, _rows(1, 60000, F, 900 + i)) for i in range(4)]
+    t_small, phi_small = wdf.server_submit(srv, 1, _rows(1, 1, F, 999))
+    wdf.server_wait(srv, t_small)
+    done_big = sum(wdf.server_poll(srv, t) for t, _ in big)
+    assert done_big < len(big)
+    for t, _ in big:
+        wdf.server_wait(srv, t)
+    np.testing.assert_array_equal(phi_small, wdf.explain(ens[1], _rows(1, 1, F, 999)))
+    assert wdf.server_request_ms(srv, t_small) < max(wdf.server_request_ms(srv, t) for t, _ in big)
+    srv.close()
