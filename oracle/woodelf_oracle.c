@@ -482,7 +482,9 @@ int64_t orc_hist_size(int32_t n_trees, const int64_t *off, const int32_t *feat, 
 }
 
 /* vc[l][p_b] = |{b in B : P[l][b] = p_b}| for every leaf (Eq. "bg_shap_derivation"
- * step (d)); counts laid out per leaf in orc_leaf_table order, 2^depth bins each. */
+ * step (d)); counts laid out per leaf in orc_leaf_table order, 2^depth bins each.
+ * Threads take disjoint trees (so each writes only its own trees' counts) over blocks
+ * of rows small enough to stay in cache while every tree reads them. */
 int orc_bg_hist(int32_t n_trees, const int64_t *off, const int32_t *feat, const float *thr,
                 const int32_t *left, const int32_t *right, const float *val,
                 const float *B, int64_t m, int64_t ldb, uint64_t *counts) {
@@ -490,32 +492,32 @@ int orc_bg_hist(int32_t n_trees, const int64_t *off, const int32_t *feat, const 
     leafset_t ls;
     if (collect_leaves(&e, &ls)) { free_leaves(&ls); return -1; }
     const int64_t hs = ls.hist_size;
+    const int64_t rows_per_block = 2048;
     memset(counts, 0, sizeof(uint64_t) * (size_t)hs);
     int err = 0;
 #pragma omp parallel
     {
-        uint64_t *mine = (uint64_t *)calloc((size_t)hs, sizeof(uint64_t));
         uint64_t *pat = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)ls.max_tree_nodes);
         int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)ls.max_tree_nodes);
-        if (!mine || !pat || !queue) err = 1;
+        if (!pat || !queue) {
+#pragma omp atomic write
+            err = 1;
+        }
+        for (int64_t r0 = 0; r0 < m; r0 += rows_per_block) {
+            const int64_t r1 = r0 + rows_per_block < m ? r0 + rows_per_block : m;
 #pragma omp for schedule(static)
-        for (int64_t r = 0; r < m; ++r) {
-            if (!mine || !pat || !queue) continue;
-            const float *x = B + r * ldb;
             for (int t = 0; t < n_trees; ++t) {
-                row_patterns(&e, t, x, pat, queue);
-                int64_t o = off[t], sz = off[t + 1] - off[t];
-                for (int64_t v = 0; v < sz; ++v) {
-                    int32_t li = ls.leaf_of_node[o + v];
-                    if (li >= 0) mine[ls.v[li].hoff + (int64_t)pat[v]] += 1;
+                if (!pat || !queue) continue;
+                const int64_t o = off[t], sz = off[t + 1] - off[t];
+                for (int64_t r = r0; r < r1; ++r) {
+                    row_patterns(&e, t, B + r * ldb, pat, queue);
+                    for (int64_t v = 0; v < sz; ++v) {
+                        int32_t li = ls.leaf_of_node[o + v];
+                        if (li >= 0) counts[ls.v[li].hoff + (int64_t)pat[v]] += 1;
+                    }
                 }
             }
         }
-#pragma omp critical
-        {
-            if (mine) for (int64_t i = 0; i < hs; ++i) counts[i] += mine[i];
-        }
-        free(mine);
         free(pat);
         free(queue);
     }
