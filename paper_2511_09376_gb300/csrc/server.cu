@@ -38,6 +38,9 @@ wdf_status fail(wdf_status s, const std::string &msg) {
 
 constexpr int64_t kPartRows = 8192;         // rows per part of a request
 constexpr int64_t kWaveWork = 16ll << 20;    // row-trees per wave (rows x trees of the ensemble)
+constexpr int64_t kSmallWork = 1ll << 20;    // largest request (row-trees) of the express slot
+constexpr int64_t kExpressWaveWork = 4ll << 20;  // row-trees per express wave: short waves
+constexpr int kMaxSkips = 8;                 // fills that may pass over a request that does not fit
 
 struct Request {
     uint64_t ticket = 0;
@@ -49,6 +52,7 @@ struct Request {
     Clock::time_point t_submit;
     int64_t next = 0;      // first row not yet in a wave
     int64_t finished = 0;  // rows whose wave has completed
+    int skips = 0;         // fills in a row that passed it over for lack of device memory
     bool failed = false;
 };
 
@@ -68,6 +72,7 @@ struct Wave {
     std::vector<Part> parts;
     int slot = -1;
     int64_t bytes = 0;
+    bool failed = false;  // a launch step failed: its parts are reported failed
 };
 
 }  // namespace
@@ -87,6 +92,7 @@ struct wdf_server {
     std::map<uint64_t, Request> active;  // submitted and not yet complete
     std::deque<uint64_t> pending;        // tickets with rows not yet in a wave, in arrival order
     std::map<uint64_t, int> state;       // 0 queued, 1 in flight, 2 done, 3 failed
+    std::map<uint64_t, double> done_ms;  // latency of each completed request
     uint64_t next_ticket = 1;
     int64_t in_use = 0;
     bool stop = false;
@@ -101,21 +107,34 @@ namespace {
 
 void run(wdf_server *s);
 
-// Launch one wave on its slot (called by the worker without the lock held).
-cudaError_t launch_wave(wdf_server *s, Wave &w) {
+// Launch one wave on its slot (called by the worker without the lock held).  If a step
+// fails part-way, the device buffers already taken are released in stream order (after
+// whatever copies were already queued) and the slot's event is still recorded, so the
+// caller reports the wave's parts only after the slot's stream has finished with their
+// host buffers.  recorded is false only if even the event could not be recorded; the
+// stream has then been synchronised before returning.
+cudaError_t launch_wave(wdf_server *s, Wave &w, bool *recorded) {
     cudaStream_t st = s->stream[(size_t)w.slot];
     std::vector<int32_t> idx;
     std::vector<const float *> C;
     std::vector<float *> phi;
     std::vector<int64_t> n, ldc, ldp;
+    cudaError_t err = cudaSuccess;
     for (Part &r : w.parts) {
         const size_t row_bytes = (size_t)r.F * sizeof(float);
-        cudaError_t e = cudaMallocAsync((void **)&r.d_C, r.n * row_bytes, st);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&r.d_phi, r.n * row_bytes, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(r.d_C, row_bytes, r.C, (size_t)r.ldc * sizeof(float), row_bytes, (size_t)r.n,
-                                  cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return e;
+        err = cudaMallocAsync((void **)&r.d_C, r.n * row_bytes, st);
+        if (err != cudaSuccess) {
+            r.d_C = nullptr;
+            break;
+        }
+        err = cudaMallocAsync((void **)&r.d_phi, r.n * row_bytes, st);
+        if (err != cudaSuccess) {
+            r.d_phi = nullptr;
+            break;
+        }
+        err = cudaMemcpy2DAsync(r.d_C, row_bytes, r.C, (size_t)r.ldc * sizeof(float), row_bytes, (size_t)r.n,
+                                cudaMemcpyHostToDevice, st);
+        if (err != cudaSuccess) break;
         idx.push_back(r.ens);
         C.push_back(r.d_C);
         phi.push_back(r.d_phi);
@@ -123,22 +142,29 @@ cudaError_t launch_wave(wdf_server *s, Wave &w) {
         ldc.push_back(r.F);
         ldp.push_back(r.F);
     }
-    const wdf_status bs = wdf_batch_explain(s->batch[(size_t)w.slot], (int32_t)idx.size(), idx.data(), C.data(),
-                                            n.data(), ldc.data(), phi.data(), ldp.data(), st);
-    if (bs != WDF_OK) {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->error = wdf_last_error();
-        return cudaErrorUnknown;
+    if (err == cudaSuccess) {
+        const wdf_status bs = wdf_batch_explain(s->batch[(size_t)w.slot], (int32_t)idx.size(), idx.data(), C.data(),
+                                                n.data(), ldc.data(), phi.data(), ldp.data(), st);
+        if (bs != WDF_OK) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->error = wdf_last_error();
+            err = cudaErrorUnknown;
+        }
     }
     for (Part &r : w.parts) {
-        const size_t row_bytes = (size_t)r.F * sizeof(float);
-        cudaError_t e = cudaMemcpy2DAsync(r.phi, (size_t)r.ldp * sizeof(float), r.d_phi, row_bytes, row_bytes,
-                                          (size_t)r.n, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaFreeAsync(r.d_C, st);
-        if (e == cudaSuccess) e = cudaFreeAsync(r.d_phi, st);
-        if (e != cudaSuccess) return e;
+        if (err == cudaSuccess) {
+            const size_t row_bytes = (size_t)r.F * sizeof(float);
+            err = cudaMemcpy2DAsync(r.phi, (size_t)r.ldp * sizeof(float), r.d_phi, row_bytes, row_bytes,
+                                    (size_t)r.n, cudaMemcpyDeviceToHost, st);
+        }
+        // released in stream order whatever happened above
+        if (r.d_C) cudaFreeAsync(r.d_C, st);
+        if (r.d_phi) cudaFreeAsync(r.d_phi, st);
+        r.d_C = r.d_phi = nullptr;
     }
-    return cudaEventRecord(s->done_ev[(size_t)w.slot], st);
+    *recorded = cudaEventRecord(s->done_ev[(size_t)w.slot], st) == cudaSuccess;
+    if (!*recorded) cudaStreamSynchronize(st);
+    return err;
 }
 
 // A part's rows are done (ok or failed): the request completes with its last part.
@@ -150,29 +176,53 @@ void finish_part(wdf_server *s, const Part &p, bool ok, Clock::time_point now) {
     if (!ok) r.failed = true;
     if (r.finished < r.n) return;
     s->state[r.ticket] = r.failed ? 3 : 2;
-    s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r.t_submit).count());
+    const double ms = std::chrono::duration<double, std::milli>(now - r.t_submit).count();
+    s->lat_ms.push_back(ms);
+    s->done_ms[r.ticket] = ms;
     s->rows_done += r.n;
     ++s->completed;
     s->active.erase(it);
 }
 
-// Fill a wave for a free slot from the queue, one part per request per pass.
+// Work of a request's remaining rows in row-trees (rows x trees of its ensemble).
+int64_t remaining_work(const wdf_server *s, const Request &r) {
+    return (r.n - r.next) * (int64_t)s->ens[(size_t)r.ens]->pk.T;
+}
+
+// Fill a wave for a free slot from the queue, one part per request per pass.  The
+// express slot (slot 0 when there are two or more) takes only requests whose remaining
+// work is at most kSmallWork, in waves of at most kExpressWaveWork, so a small request
+// never waits behind the large parts that occupy the other slots.  A part that does not fit the remaining device budget is
+// skipped (a smaller one further back may fit), but once a request has been passed over
+// kMaxSkips times the fill stops at it, so that memory frees up for it and a stream of
+// narrow requests cannot hold a wide one back indefinitely.
 Wave fill_wave(wdf_server *s, int slot) {
     Wave w;
     w.slot = slot;
+    const bool express = s->n_slots >= 2 && slot == 0;
+    const int64_t wave_work = express ? kExpressWaveWork : kWaveWork;
     int64_t work = 0;
-    bool added = true;
-    while (added && (int)w.parts.size() < s->max_wave && work < kWaveWork) {
+    bool added = true, blocked = false;
+    while (added && !blocked && (int)w.parts.size() < s->max_wave && work < wave_work) {
         added = false;
         for (auto it = s->pending.begin();
-             it != s->pending.end() && (int)w.parts.size() < s->max_wave && work < kWaveWork;) {
+             it != s->pending.end() && (int)w.parts.size() < s->max_wave && work < wave_work;) {
             Request &r = s->active[*it];
+            if (express && remaining_work(s, r) > kSmallWork) {
+                ++it;
+                continue;
+            }
             const int64_t rows = std::min(kPartRows, r.n - r.next);
             const int64_t bytes = 2 * rows * (int64_t)r.F * (int64_t)sizeof(float);
             if (s->in_use + w.bytes + bytes > s->budget) {
+                if (++r.skips > kMaxSkips) {
+                    blocked = true;
+                    break;
+                }
                 ++it;  // does not fit now; a smaller part further back may
                 continue;
             }
+            r.skips = 0;
             Part p;
             p.ticket = r.ticket;
             p.ens = r.ens;
@@ -213,7 +263,7 @@ void run(wdf_server *s) {
                 continue;
             }
             const auto now = Clock::now();
-            for (const Part &p : w.parts) finish_part(s, p, q == cudaSuccess, now);
+            for (const Part &p : w.parts) finish_part(s, p, q == cudaSuccess && !w.failed, now);
             if (q != cudaSuccess) s->error = std::string("wave failed: ") + cudaGetErrorString(q);
             s->t_last = now;
             s->in_use -= w.bytes;
@@ -225,16 +275,24 @@ void run(wdf_server *s) {
         for (int k = 0; k < s->n_slots && !s->pending.empty(); ++k) {
             if (!s->wave[(size_t)k].parts.empty()) continue;
             Wave w = fill_wave(s, k);
-            if (w.parts.empty()) break;  // no part fits until memory frees up
+            if (w.parts.empty()) {
+                if (s->n_slots >= 2 && k == 0) continue;  // no small request queued: try the other slots
+                break;                                    // no part fits until memory frees up
+            }
             s->in_use += w.bytes;
             ++s->waves;
             lk.unlock();
-            const cudaError_t e = launch_wave(s, w);
+            bool recorded = true;
+            const cudaError_t e = launch_wave(s, w, &recorded);
             lk.lock();
             if (e != cudaSuccess) {
-                s->error = std::string("launch failed: ") + cudaGetErrorString(e);
+                if (s->error.empty() || e != cudaErrorUnknown)
+                    s->error = std::string("launch failed: ") + cudaGetErrorString(e);
+                w.failed = true;
+            }
+            if (!recorded) {  // the stream was synchronised: report the parts now
                 const auto now = Clock::now();
-                for (const Part &p : w.parts) finish_part(s, p, false, now);
+                for (const Part &p : w.parts) finish_part(s, p, !w.failed, now);
                 s->in_use -= w.bytes;
                 s->cv_done.notify_all();
                 continue;
@@ -365,6 +423,15 @@ wdf_status wdf_server_poll(wdf_server *s, uint64_t ticket, int32_t *done) {
     if (it == s->state.end()) return fail(WDF_EINVAL, "unknown ticket");
     *done = it->second >= 2 ? 1 : 0;
     if (it->second == 3) return fail(WDF_ECUDA, s->error);
+    return WDF_OK;
+}
+
+wdf_status wdf_server_request_ms(wdf_server *s, uint64_t ticket, double *ms) {
+    if (!s || !ms) return fail(WDF_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->done_ms.find(ticket);
+    if (it == s->done_ms.end()) return fail(WDF_EINVAL, "unknown or unfinished ticket");
+    *ms = it->second;
     return WDF_OK;
 }
 
