@@ -160,9 +160,9 @@ wdf_status wdf_set_metric(wdf_ensemble *ens, wdf_metric metric);
  * phi[c, i] for the n consumer rows C (leading dimension ldc) into phi (leading
  * dimension ldphi >= F): Algorithm 3 step 4 / Eq. "bg_shap_derivation" step (g).
  * C and phi live in the same memory kind.  WDF_EINVAL if no background was set.
- * Device kind: asynchronous; the rows' decision codes (one or two bytes per code column
- * and row, at most 2^20 rows at a time) live in a temporary stream-ordered allocation,
- * so calls on different streams never share scratch memory.  Host kind: copies
+ * Device kind: asynchronous and allocation-free: every block computes its rows'
+ * decision codes in shared memory, so calls on different streams share no scratch
+ * memory.  Host kind: copies
  * through the ensemble's device staging buffers and returns once phi is written on the
  * host.  phi of a row does not depend on the other rows of the call (the same
  * floating-point additions in the same order).
@@ -194,8 +194,11 @@ wdf_status wdf_expected_value(const wdf_ensemble *ens, double *out, void *stream
  * Global attribution over n explained rows (device pointers): mean_abs[i] =
  * (1/n) sum_c |phi[c,i]| and mean[i] = (1/n) sum_c phi[c,i], accumulated in FP64 in a
  * fixed order (the paper's global attribution combines many local attributions,
- * section "Introduction").  mean_abs and mean are device arrays of F doubles.
- * Asynchronous.
+ * section "Introduction"), so the result does not depend on scheduling.  With packed
+ * rows (ldphi == n_features <= 512, 16-byte aligned phi) short runs of 8 values are
+ * first summed as exact-error FP32 pairs (TwoSum; within 2^-42 of the run's exact sum)
+ * and each pair is then added in FP64.  mean_abs and mean are device arrays of F
+ * doubles.  Asynchronous.
  */
 wdf_status wdf_global_attribution(wdf_ctx *ctx, const float *phi, int64_t n, int64_t ldphi, int32_t n_features,
                                   double *mean_abs, double *mean, void *stream);
@@ -241,13 +244,22 @@ wdf_status wdf_batch_tile_rows(const wdf_batch *batch, int32_t depth, int32_t *t
  * work, or the next part's device buffers (2 * rows * F * 4 bytes) would exceed
  * device_budget_bytes; it runs the wave as copies in, ONE batch launch
  * (wdf_batch_explain) and copies out on the slot's stream.  Waves of different slots
- * overlap on the GPU.  A request completes with its last part.  Every ensemble must have
- * its background set and must outlive the server.  A request's phi equals what
- * wdf_explain gives for the same rows, whatever shares its waves.
+ * overlap on the GPU.  With two or more slots, slot 0 is an express slot: it takes only
+ * requests of at most 2^20 rows x trees of remaining work, in waves of at most 2^22
+ * rows x trees, so small requests do not queue behind large parts.  A request whose next part does not fit the remaining
+ * budget is passed over for smaller ones at most 8 fills in a row; then the fill stops
+ * at it until memory frees up.  A request completes with its last part.  Every ensemble
+ * must have its background set and must outlive the server.  A request's phi equals
+ * what wdf_explain gives for the same rows, whatever shares its waves.
  * wdf_server_submit: C (n x F, row stride ldc) is read and phi (row stride ldphi)
  * written asynchronously: both must stay valid until wdf_server_wait / _poll reports the
  * ticket done.  WDF_ENOMEM if one part of the request (min(n, 8192) rows) alone exceeds
- * the budget, WDF_EBUSY while shutting down.  wdf_server_wait: WDF_ETIMEOUT if not done within timeout_ms.
+ * the budget, WDF_EBUSY while shutting down.  wdf_server_wait: WDF_ETIMEOUT if not done
+ * within timeout_ms (the request stays queued or in flight).  A request whose wave
+ * failed on the device is reported done with WDF_ECUDA, only after its slot's stream
+ * has finished with its buffers.
+ * wdf_server_request_ms: the latency (submit to completion, milliseconds) of a completed
+ * request; WDF_EINVAL for an unknown or unfinished ticket.
  * wdf_server_stats: latency percentiles are over requests completed since creation or
  * the last wdf_server_reset_stats, measured from submit to completion; rows_per_s over
  * the span from the first submit to the last completion.  wdf_server_destroy finishes
@@ -266,6 +278,7 @@ wdf_status wdf_server_submit(wdf_server *server, int32_t ensemble_index, const f
                              float *phi, int64_t ldphi, uint64_t *ticket);
 wdf_status wdf_server_wait(wdf_server *server, uint64_t ticket, int64_t timeout_ms);
 wdf_status wdf_server_poll(wdf_server *server, uint64_t ticket, int32_t *done);
+wdf_status wdf_server_request_ms(wdf_server *server, uint64_t ticket, double *ms);
 wdf_status wdf_server_stats(wdf_server *server, wdf_serving_stats *out);
 wdf_status wdf_server_reset_stats(wdf_server *server);
 void wdf_server_destroy(wdf_server *server);
@@ -284,7 +297,8 @@ void wdf_server_destroy(wdf_server *server);
  * about 4.2 million rows).  Calls share that array and it keeps the last call's
  * contents: calls that overlap on the GPU race and must be ordered (e.g. one stream).
  * The first call on a device looks up the array's address with that device current;
- * make it before any stream capture begins.  Asynchronous.
+ * make it before any stream capture begins.  stream must belong to `device`.
+ * Asynchronous.
  */
 wdf_status wdf_global_attribution_noalloc(int32_t device, const float *phi, int64_t n, int64_t ldphi,
                                           int32_t n_features, double *mean_abs, double *mean, void *stream);
@@ -305,6 +319,17 @@ wdf_status wdf_global_attribution_noalloc(int32_t device, const float *phi, int6
  */
 wdf_status wdf_debug_leaf_hist(const wdf_ensemble *ens, uint32_t *out, int64_t out_elems);
 wdf_status wdf_debug_pair_table(wdf_ctx *ctx, int32_t depth, const int32_t *first, wdf_metric metric, double *out);
+
+/* Failure-detection hook for tests (process-wide, not thread-safe against concurrent
+ * contractions): the first mbarrier wait of every CTA of later tensor-core contractions
+ * polls at most `polls` times (polls <= 0 restores the normal limit of 2^22 polls).  A
+ * wait that gives up makes wdf_set_background (or wdf_set_background_counts,
+ * wdf_set_path_dependent) return WDF_ETIMEOUT with the background left unset; the kernel
+ * still waits at the normal limit for its own tensor-core work before it frees its
+ * tensor memory and returns, so the context stays usable.  The paper has no
+ * counterpart: this exists so that the bounded waits can be shown to end in an error
+ * status without faulting or hanging the GPU. */
+void wdf_debug_contract_wait_limit(int32_t polls);
 
 /* Number of kernels this library has launched in the process so far (all devices).
  * Benchmarks read it before and after a timed region. */

@@ -61,6 +61,8 @@ _lib.wdf_ensemble_destroy.argtypes = [_vp]
 _lib.wdf_ensemble_destroy.restype = None
 _lib.wdf_batch_destroy.argtypes = [_vp]
 _lib.wdf_batch_destroy.restype = None
+_lib.wdf_debug_contract_wait_limit.argtypes = [_c.c_int32]
+_lib.wdf_debug_contract_wait_limit.restype = None
 
 
 class WdfError(RuntimeError):
@@ -316,6 +318,12 @@ def debug_pair_table(ctx: Context, first, metric="shapley") -> np.ndarray:
     return out
 
 
+def debug_contract_wait_limit(polls: int) -> None:
+    """Test hook: poll limit of the first mbarrier wait of every CTA of later tensor-core
+    contractions (0 restores the normal limit)."""
+    _lib.wdf_debug_contract_wait_limit(int(polls))
+
+
 def set_metric(e: Ensemble, metric="shapley") -> None:
     """'shapley' (default) or 'banzhaf'; the background must be set again afterwards."""
     _check(_lib.wdf_set_metric(e.handle, _METRIC[metric]))
@@ -397,10 +405,11 @@ _lib.wdf_server_submit.argtypes = [_vp, _c.c_int32, _vp, _c.c_int64, _c.c_int64,
                                    _c.POINTER(_c.c_uint64)]
 _lib.wdf_server_wait.argtypes = [_vp, _c.c_uint64, _c.c_int64]
 _lib.wdf_server_poll.argtypes = [_vp, _c.c_uint64, _c.POINTER(_c.c_int32)]
+_lib.wdf_server_request_ms.argtypes = [_vp, _c.c_uint64, _c.POINTER(_c.c_double)]
 _lib.wdf_server_stats.argtypes = [_vp, _vp]
 _lib.wdf_server_reset_stats.argtypes = [_vp]
 for _f in ("wdf_server_create", "wdf_server_submit", "wdf_server_wait", "wdf_server_poll", "wdf_server_stats",
-           "wdf_server_reset_stats"):
+           "wdf_server_reset_stats", "wdf_server_request_ms"):
     getattr(_lib, _f).restype = _c.c_int
 _lib.wdf_server_destroy.argtypes = [_vp]
 _lib.wdf_server_destroy.restype = None
@@ -442,15 +451,20 @@ def server_create(ctx: Context, ensembles, device_budget_bytes: int, n_slots: in
 
 
 def server_submit(server: Server, ensemble_index: int, C, phi=None):
-    """Queue one request (host float32 rows).  Returns (ticket, phi array filled when done)."""
-    C = np.ascontiguousarray(C, dtype=np.float32)
+    """Queue one request (host float32 rows, any row stride).  Returns (ticket, phi array
+    filled when done); phi may be a row-strided float32 view."""
+    C = np.asarray(C)
+    if C.dtype != np.float32 or C.ndim != 2 or C.strides[1] != 4 or C.strides[0] % 4:
+        C = np.ascontiguousarray(C, dtype=np.float32)
     F = ensemble_info(server.ensembles[ensemble_index])["n_features"]
     if phi is None:
         phi = np.empty((C.shape[0], F), dtype=np.float32)
+    if phi.dtype != np.float32 or phi.ndim != 2 or phi.strides[1] != 4 or phi.strides[0] % 4:
+        raise ValueError("phi must be a float32 matrix with unit column stride")
     t = _c.c_uint64(0)
     _check(_lib.wdf_server_submit(server.handle, int(ensemble_index), _vp(C.ctypes.data), int(C.shape[0]),
-                                  int(C.strides[0] // 4), _vp(phi.ctypes.data), int(phi.strides[0] // 4),
-                                  _c.byref(t)))
+                                  int(max(C.strides[0] // 4, C.shape[1])), _vp(phi.ctypes.data),
+                                  int(max(phi.strides[0] // 4, phi.shape[1])), _c.byref(t)))
     server._live[t.value] = (C, phi)
     return t.value, phi
 
@@ -466,6 +480,13 @@ def server_poll(server: Server, ticket: int) -> bool:
     if d.value:
         server._live.pop(ticket, None)
     return bool(d.value)
+
+
+def server_request_ms(server: Server, ticket: int) -> float:
+    """Latency (submit to completion, ms) of a completed request."""
+    v = _c.c_double(0.0)
+    _check(_lib.wdf_server_request_ms(server.handle, _c.c_uint64(ticket), _c.byref(v)))
+    return v.value
 
 
 def server_stats(server: Server) -> dict:

@@ -83,16 +83,20 @@ void free_ensemble(wdf_ensemble *e) {
     dfree(e->d_nodes); dfree(e->d_keys); dfree(e->d_group_leaf); dfree(e->d_leaf_row);
     dfree(e->d_w_rows); dfree(e->d_tiles); dfree(e->d_t32);
     dfree(e->d_rec); dfree(e->d_meta); dfree(e->d_cols); dfree(e->d_col_thr);
-    dfree(e->d_t32t); dfree(e->d_tiles128); dfree(e->d_err); dfree(e->d_A); dfree(e->d_ratio);
+    dfree(e->d_apk); dfree(e->d_bpk); dfree(e->d_tiles128); dfree(e->d_err); dfree(e->d_A); dfree(e->d_ratio);
     dfree(e->d_hist); dfree(e->d_vc); dfree(e->d_scale); dfree(e->d_S); dfree(e->d_sfold); dfree(e->d_base);
+    dfree(e->d_lines);
     for (int i = 0; i < 2; ++i) {
         dfree(e->d_codes[i]);
         dfree(e->d_stage_in[i]);
         dfree(e->d_stage_out[i]);
         if (e->ist[i]) cudaStreamDestroy(e->ist[i]);
         if (e->ev_join[i]) cudaEventDestroy(e->ev_join[i]);
+        if (e->ev_enc[i]) cudaEventDestroy(e->ev_enc[i]);
+        if (e->ev_cnt[i]) cudaEventDestroy(e->ev_cnt[i]);
         e->ist[i] = nullptr;
         e->ev_join[i] = nullptr;
+        e->ev_enc[i] = e->ev_cnt[i] = nullptr;
     }
     if (e->ev_fork) cudaEventDestroy(e->ev_fork);
     e->ev_fork = nullptr;
@@ -101,15 +105,23 @@ void free_ensemble(wdf_ensemble *e) {
 // Double-buffered staging for host-memory calls: chunk i of the rows goes through
 // buffer i % 2 on internal stream i % 2, so the copy engines of one chunk overlap the
 // kernels of the other.  Grows to the largest chunk seen (at most kStageRows rows).
-wdf_status ensure_staging(wdf_ensemble *e, int64_t rows, bool out) {
-    rows = std::min(rows, kStageRows);
+wdf_status ensure_streams(wdf_ensemble *e) {
     if (!e->ist[0]) {
         for (int i = 0; i < 2; ++i) {
             WDF_CUDA(cudaStreamCreateWithFlags(&e->ist[i], cudaStreamNonBlocking));
             WDF_CUDA(cudaEventCreateWithFlags(&e->ev_join[i], cudaEventDisableTiming));
+            WDF_CUDA(cudaEventCreateWithFlags(&e->ev_enc[i], cudaEventDisableTiming));
+            WDF_CUDA(cudaEventCreateWithFlags(&e->ev_cnt[i], cudaEventDisableTiming));
         }
         WDF_CUDA(cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming));
     }
+    return WDF_OK;
+}
+
+wdf_status ensure_staging(wdf_ensemble *e, int64_t rows, bool out) {
+    rows = std::min(rows, kStageRows);
+    wdf_status s0 = ensure_streams(e);
+    if (s0 != WDF_OK) return s0;
     if (rows > e->stage_rows) {
         WDF_CUDA(cudaDeviceSynchronize());
         for (int i = 0; i < 2; ++i) {
@@ -145,30 +157,52 @@ wdf_status ensure_codes(wdf_ensemble *e, int64_t rows, int nbuf) {
     return WDF_OK;
 }
 
-// K-major tables, 128-row tiles and the error flag for the tensor-core contraction.
-wdf_status ensure_tensor_core_state(wdf_ensemble *e) {
-    if (e->d_t32t) return WDF_OK;
+// Counts of device rows B (m rows) added into hist: with more than one chunk of codes,
+// the encode of the next chunk overlaps the count of this one (two code buffers, the
+// side stream ist[0]).
+wdf_status count_device_rows(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, uint32_t *hist,
+                             cudaStream_t st) {
+    const wdf::Packed &p = ens->pk;
+    const bool overlap = m > kCodeRows;
+    wdf_status s = ensure_codes(ens, m, overlap ? 2 : 1);
+    if (s == WDF_OK && overlap) s = ensure_streams(ens);
+    if (s != WDF_OK) return s;
+    wdf::BgOverlap ov{ens->d_codes[1], ens->ist[0], {ens->ev_enc[0], ens->ev_enc[1]}, {ens->ev_cnt[0], ens->ev_cnt[1]}};
+    WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, ens->arrays(), p.T, ens->d_codes[0], ens->code_rows, hist,
+                                 ens->ctx->dev, st, overlap ? &ov : nullptr));
+    return WDF_OK;
+}
+
+// Split operand stages, 128-row tiles and the error flag for the tensor-core
+// contraction in split mode `mode`: the tiles, the flag and the A stages (room for any
+// mode) once, the B stages (the tables split for this mode) whenever the mode changes.
+wdf_status ensure_tensor_core_state(wdf_ensemble *e, int mode) {
     const wdf::Packed &p = e->pk;
-    const int K = 1 << p.D, N = p.D << p.D;
-    std::vector<int4> tiles;
-    for (int gi = 0; gi < e->G; ++gi)
-        for (int r0 = p.group_off[(size_t)gi]; r0 < p.group_off[(size_t)gi + 1]; r0 += 128)
-            tiles.push_back(make_int4(gi, r0, std::min(r0 + 128, p.group_off[(size_t)gi + 1]), 0));
-    float *t32t = nullptr;
-    WDF_CUDA(dalloc(&t32t, (size_t)e->G * K * N, &e->bytes));
-    WDF_CUDA(dalloc(&e->d_tiles128, tiles.size(), &e->bytes));
-    WDF_CUDA(dalloc(&e->d_err, 1, &e->bytes));
-    WDF_CUDA(cudaMemset(e->d_err, 0, sizeof(int)));
-    if (!tiles.empty())
-        WDF_CUDA(cudaMemcpy(e->d_tiles128, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    float *scratch = nullptr;
-    WDF_CUDA(dalloc(&scratch, (size_t)e->G * K * N, &e->bytes));
-    WDF_CUDA(wdf::launch_tables(p.D, e->metric, e->d_keys, e->G, scratch, nullptr, t32t, 0));
-    WDF_CUDA(cudaStreamSynchronize(0));
-    cudaFree(scratch);
-    e->bytes -= (int64_t)((size_t)e->G * K * N * sizeof(float));
-    e->d_t32t = t32t;
-    e->n_tiles128 = (int)tiles.size();
+    if (!e->d_tiles128) {
+        std::vector<int4> tiles;
+        for (int gi = 0; gi < e->G; ++gi)
+            for (int r0 = p.group_off[(size_t)gi]; r0 < p.group_off[(size_t)gi + 1]; r0 += 128)
+                tiles.push_back(make_int4(gi, r0, std::min(r0 + 128, p.group_off[(size_t)gi + 1]), 0));
+        WDF_CUDA(dalloc(&e->d_tiles128, std::max<size_t>(tiles.size(), 1), &e->bytes));
+        WDF_CUDA(dalloc(&e->d_err, 1, &e->bytes));
+        WDF_CUDA(cudaMemset(e->d_err, 0, sizeof(int)));
+        if (!tiles.empty())
+            WDF_CUDA(cudaMemcpy(e->d_tiles128, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        e->n_tiles128 = (int)tiles.size();
+        WDF_CUDA(dalloc(&e->d_apk, std::max<size_t>(wdf::contract_tc_a_bytes(p.D, e->n_tiles128), 16), &e->bytes));
+    }
+    if (e->bpk_mode != mode) {
+        if (e->d_bpk) {
+            WDF_CUDA(cudaDeviceSynchronize());  // an earlier contraction may still read it
+            e->bytes -= (int64_t)wdf::contract_tc_b_bytes(p.D, e->bpk_mode, e->G);
+            dfree(e->d_bpk);
+        }
+        e->bpk_mode = -1;
+        WDF_CUDA(dalloc(&e->d_bpk, std::max<size_t>(wdf::contract_tc_b_bytes(p.D, mode, e->G), 16), &e->bytes));
+        WDF_CUDA(wdf::launch_pack_b(p.D, mode, e->d_t32, e->G, e->d_bpk, 0));
+        WDF_CUDA(cudaStreamSynchronize(0));
+        e->bpk_mode = mode;
+    }
     return WDF_OK;
 }
 
@@ -199,10 +233,11 @@ wdf_status ensure_frequency_state(wdf_ensemble *ens, wdf_precision precision) {
         WDF_CUDA(dalloc(&ens->d_scale, (size_t)ens->n_live, &ens->bytes));
         WDF_CUDA(dalloc(&ens->d_S, (size_t)ens->n_live * N, &ens->bytes));
         WDF_CUDA(dalloc(&ens->d_sfold, hist_n * wdf::slot_pad(p.D), &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_lines, (size_t)p.T * wdf::lines_words(p.D), &ens->bytes));
         WDF_CUDA(dalloc(&ens->d_base, 1, &ens->bytes));
     }
     ens->has_bg = 0;
-    if (precision != WDF_FP32) return ensure_tensor_core_state(ens);
+    if (precision != WDF_FP32) return ensure_tensor_core_state(ens, tc_mode(precision));
     return WDF_OK;
 }
 
@@ -215,15 +250,17 @@ wdf_status contract_and_fold(wdf_ensemble *ens, wdf_precision precision, cudaStr
         WDF_CUDA(wdf::launch_contract_fp32(p.D, ens->d_A, ens->d_scale, ens->d_tiles, ens->n_tiles, ens->d_t32,
                                            ens->d_S, st));
     } else {
-        WDF_CUDA(wdf::launch_contract_tc(p.D, tc_mode(precision), ens->d_A, ens->d_scale,
-                                         ens->d_tiles128, ens->n_tiles128, ens->d_t32t, ens->d_S, ens->d_err, st));
+        // the flag may hold an expiry of an earlier call: clear it first
+        WDF_CUDA(cudaMemsetAsync(ens->d_err, 0, sizeof(int), st));
+        WDF_CUDA(wdf::launch_contract_tc(p.D, tc_mode(precision), ens->d_A, ens->d_scale, ens->d_tiles128,
+                                         ens->n_tiles128, ens->d_apk, ens->d_bpk, ens->d_S, ens->d_err, st));
         // a bounded wait inside the kernel that expired is reported here
         int flag = 0;
         WDF_CUDA(cudaMemcpyAsync(&flag, ens->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         WDF_CUDA(cudaStreamSynchronize(st));
         if (flag) return fail(WDF_ETIMEOUT, "tensor-core contraction: an mbarrier wait expired");
     }
-    WDF_CUDA(wdf::launch_fold(p.D, ens->d_S, ens->d_leaf_row, p.T, ens->d_sfold, st));
+    WDF_CUDA(wdf::launch_fold(p.D, ens->d_S, ens->d_leaf_row, p.T, ens->d_lines, ens->d_sfold, st));
     return WDF_OK;
 }
 
@@ -234,6 +271,7 @@ wdf_status finish_background(wdf_ensemble *ens, int64_t m, wdf_precision precisi
     WDF_CUDA(wdf::launch_leaf_counts(p.D, ens->d_hist, ens->d_group_leaf, ens->n_live, ens->d_vc, ens->d_A, st));
     WDF_CUDA(wdf::launch_scale(ens->d_w_rows, ens->n_live, m, ens->d_scale, st));
     WDF_CUDA(wdf::launch_base_value(p.D, ens->d_vc, nullptr, ens->d_w_rows, ens->n_live, m, ens->d_base, st));
+    WDF_CUDA(wdf::launch_line_maps(p.D, ens->d_hist, p.T, ens->d_lines, st));
     wdf_status s1 = contract_and_fold(ens, precision, st);
     if (s1 != WDF_OK) return s1;
     ens->m = m;
@@ -248,7 +286,9 @@ extern "C" {
 
 const char *wdf_last_error(void) { return g_err.c_str(); }
 
-const char *wdf_version(void) { return "woodelf-gb300 0.1 (sm_103a)"; }
+const char *wdf_version(void) { return "woodelf-gb300 0.2 (sm_103a)"; }
+
+void wdf_debug_contract_wait_limit(int32_t polls) { wdf::set_contract_first_wait_limit(polls > 0 ? (uint32_t)polls : 0u); }
 
 int64_t wdf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
@@ -337,7 +377,7 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
             chk(cudaMemcpy(e->d_col_thr, p.col_thr.data(), p.col_thr.size() * 4, cudaMemcpyHostToDevice));
         if (e->n_tiles) chk(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
         // step 2 of Algorithm 3 depends only on the path signatures: build the tables now
-        chk(wdf::launch_tables(p.D, e->metric, e->d_keys, e->G, e->d_t32, nullptr, nullptr, 0));
+        chk(wdf::launch_tables(p.D, e->metric, e->d_keys, e->G, e->d_t32, nullptr, 0));
         chk(cudaStreamSynchronize(0));
     }
     if (ce != cudaSuccess) {
@@ -378,12 +418,11 @@ wdf_status wdf_set_metric(wdf_ensemble *ens, wdf_metric metric) {
     const wdf::Packed &p = ens->pk;
     ens->metric = (int)metric;
     ens->has_bg = 0;  // the folded vectors were built from the other tables
-    WDF_CUDA(wdf::launch_tables(p.D, ens->metric, ens->d_keys, ens->G, ens->d_t32, nullptr, nullptr, 0));
-    if (ens->d_t32t) {  // rebuild the tensor-core copy lazily with the new metric
-        dfree(ens->d_t32t);
-        dfree(ens->d_tiles128);
-        dfree(ens->d_err);
-        ens->n_tiles128 = 0;
+    WDF_CUDA(wdf::launch_tables(p.D, ens->metric, ens->d_keys, ens->G, ens->d_t32, nullptr, 0));
+    if (ens->d_bpk) {  // split the new tables again on the next tensor-core contraction
+        ens->bytes -= (int64_t)wdf::contract_tc_b_bytes(p.D, ens->bpk_mode, ens->G);
+        dfree(ens->d_bpk);
+        ens->bpk_mode = -1;
     }
     WDF_CUDA(cudaStreamSynchronize(0));
     return WDF_OK;
@@ -408,10 +447,8 @@ wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int6
     if (s0 != WDF_OK) return s0;
     WDF_CUDA(cudaMemsetAsync(ens->d_hist, 0, hist_n * 4, st));
     if (kind == WDF_MEM_DEVICE) {
-        wdf_status s = ensure_codes(ens, m, 1);
+        wdf_status s = count_device_rows(ens, B, m, ldb, ens->d_hist, st);
         if (s != WDF_OK) return s;
-        WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, ens->arrays(), p.T, ens->d_codes[0], ens->code_rows, ens->d_hist,
-                                     ens->ctx->dev, st));
     } else {
         wdf_status s = ensure_staging(ens, m, false);
         if (s == WDF_OK) s = ensure_codes(ens, ens->stage_rows, 2);
@@ -455,11 +492,8 @@ wdf_status wdf_background_counts(wdf_ensemble *ens, const float *B, int64_t m, i
     DeviceGuard g(ens->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const wdf::Packed &p = ens->pk;
-    wdf_status s = ensure_codes(ens, m, 1);
-    if (s != WDF_OK) return s;
-    WDF_CUDA(wdf::launch_bg_hist(p.D, B, m, ldb, ens->arrays(), p.T, ens->d_codes[0], ens->code_rows, counts,
-                                 ens->ctx->dev, st));
-    return WDF_OK;
+    (void)p;
+    return count_device_rows(ens, B, m, ldb, counts, st);
 }
 
 wdf_status wdf_set_background_counts(wdf_ensemble *ens, const uint32_t *counts, int64_t m_total,
@@ -506,6 +540,7 @@ wdf_status wdf_set_path_dependent(wdf_ensemble *ens, wdf_precision precision, vo
     WDF_CUDA(wdf::launch_pd_freq(p.D, ens->d_ratio, ens->n_live, ens->d_A, st));
     WDF_CUDA(wdf::launch_scale(ens->d_w_rows, ens->n_live, 1, ens->d_scale, st));
     WDF_CUDA(wdf::launch_base_value(p.D, nullptr, ens->d_ratio, ens->d_w_rows, ens->n_live, 1, ens->d_base, st));
+    WDF_CUDA(wdf::launch_line_maps(p.D, nullptr, p.T, ens->d_lines, st));
     wdf_status s1 = contract_and_fold(ens, precision, st);
     if (s1 != WDF_OK) return s1;
     ens->m = 0;
@@ -606,7 +641,7 @@ wdf_status wdf_global_attribution(wdf_ctx *ctx, const float *phi, int64_t n, int
     if (n > 0 && !phi) return fail(WDF_EINVAL, "phi is null");
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t pn = (size_t)wdf::global_attr_blocks(n) * n_features * 2;
+    const size_t pn = (size_t)wdf::global_attr_partial_doubles(n, n_features);
     double *partial = nullptr;
     WDF_CUDA(cudaMallocAsync((void **)&partial, pn * sizeof(double), st));
     cudaError_t e = wdf::launch_global_attr(phi, n, ldphi, n_features, partial, mean_abs, mean, st);
@@ -659,7 +694,7 @@ wdf_status wdf_debug_pair_table(wdf_ctx *ctx, int32_t depth, const int32_t *firs
     if (ce == cudaSuccess) ce = dalloc(&d_t32, K * N, &dummy);
     if (ce == cudaSuccess) ce = dalloc(&d_t64, K * N, &dummy);
     if (ce == cudaSuccess) ce = cudaMemcpy(d_key, &key, 4, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = wdf::launch_tables(depth, (int)metric, d_key, 1, d_t32, d_t64, nullptr, 0);
+    if (ce == cudaSuccess) ce = wdf::launch_tables(depth, (int)metric, d_key, 1, d_t32, d_t64, 0);
     if (ce == cudaSuccess) ce = cudaMemcpy(out, d_t64, K * N * sizeof(double), cudaMemcpyDeviceToHost);
     dfree(d_key);
     dfree(d_t32);

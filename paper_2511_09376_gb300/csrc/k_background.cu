@@ -228,26 +228,52 @@ static cudaError_t bg_hist_d(const unsigned char *codes, int64_t m, const TreeAr
     }
 }
 
+template <int D>
+static cudaError_t bg_count_chunk(const unsigned char *codes, int64_t rows, const TreeArrays &ta, int T,
+                                  uint32_t *hist, const DevInfo &dev, cudaStream_t st) {
+    return bg_hist_d<D>(codes, rows, ta, T, hist, dev, st);
+}
+
 cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, const TreeArrays &ta, int T,
                            unsigned char *codes, int64_t code_rows, uint32_t *hist, const DevInfo &dev,
-                           cudaStream_t st) {
+                           cudaStream_t st, const BgOverlap *ov) {
     if (m == 0) return cudaSuccess;
     if (code_rows < kBgMaxTileRows || code_rows % kBgMaxTileRows) return cudaErrorInvalidValue;
-    for (int64_t r0 = 0; r0 < m; r0 += code_rows) {
+    cudaError_t err = cudaSuccess;
+    if (ov) {
+        // the side stream starts after everything already queued on st (B, the zeroed counts)
+        err = cudaEventRecord(ov->cnt[0], st);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(ov->side, ov->cnt[0], 0);
+        if (err != cudaSuccess) return err;
+    }
+    int64_t k = 0;
+    for (int64_t r0 = 0; r0 < m; r0 += code_rows, ++k) {
         const int64_t rows = std::min(code_rows, m - r0);
         const int64_t rows_pad = (rows + kBgMaxTileRows - 1) / kBgMaxTileRows * kBgMaxTileRows;
-        cudaError_t err = launch_encode_codes(B + r0 * ldb, rows, ldb, ta, rows_pad, codes, st);
+        const int b = ov ? (int)(k & 1) : 0;
+        unsigned char *buf = b ? ov->codes1 : codes;
+        if (ov) {
+            // encode chunk k on the side stream once the count of chunk k - 2 (the last
+            // reader of this buffer) is done; the count of chunk k waits for the encode
+            if (k >= 2) err = cudaStreamWaitEvent(ov->side, ov->cnt[b], 0);
+            if (err == cudaSuccess) err = launch_encode_codes(B + r0 * ldb, rows, ldb, ta, rows_pad, buf, ov->side);
+            if (err == cudaSuccess) err = cudaEventRecord(ov->enc[b], ov->side);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(st, ov->enc[b], 0);
+        } else {
+            err = launch_encode_codes(B + r0 * ldb, rows, ldb, ta, rows_pad, buf, st);
+        }
         if (err != cudaSuccess) return err;
         switch (D) {
-            case 2: err = bg_hist_d<2>(codes, rows, ta, T, hist, dev, st); break;
-            case 3: err = bg_hist_d<3>(codes, rows, ta, T, hist, dev, st); break;
-            case 4: err = bg_hist_d<4>(codes, rows, ta, T, hist, dev, st); break;
-            case 5: err = bg_hist_d<5>(codes, rows, ta, T, hist, dev, st); break;
-            case 6: err = bg_hist_d<6>(codes, rows, ta, T, hist, dev, st); break;
-            case 7: err = bg_hist_d<7>(codes, rows, ta, T, hist, dev, st); break;
-            case 8: err = bg_hist_d<8>(codes, rows, ta, T, hist, dev, st); break;
+            case 2: err = bg_count_chunk<2>(buf, rows, ta, T, hist, dev, st); break;
+            case 3: err = bg_count_chunk<3>(buf, rows, ta, T, hist, dev, st); break;
+            case 4: err = bg_count_chunk<4>(buf, rows, ta, T, hist, dev, st); break;
+            case 5: err = bg_count_chunk<5>(buf, rows, ta, T, hist, dev, st); break;
+            case 6: err = bg_count_chunk<6>(buf, rows, ta, T, hist, dev, st); break;
+            case 7: err = bg_count_chunk<7>(buf, rows, ta, T, hist, dev, st); break;
+            case 8: err = bg_count_chunk<8>(buf, rows, ta, T, hist, dev, st); break;
             default: return cudaErrorInvalidValue;
         }
+        if (err == cudaSuccess && ov) err = cudaEventRecord(ov->cnt[b], st);
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;

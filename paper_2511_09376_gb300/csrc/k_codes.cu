@@ -12,7 +12,7 @@ namespace wdf {
 // along a row), then each warp encodes whole columns (lane = row).  Rows from rows to
 // the end of the last block get code 0 (never counted).
 constexpr int kEncodeThreads = 256;
-constexpr int kEncodeCols = 256;
+constexpr int kEncodeCols = 128;  // 16.5 KB of staging: fits beside a counting block
 
 __global__ void __launch_bounds__(kEncodeThreads) k_encode_codes(const float *__restrict__ X, int64_t rows,
                                                                 int64_t ldx, TreeArrays ta,

@@ -21,7 +21,7 @@ __device__ __forceinline__ double binom_small(int n, int k) {
 // (metric 1, Banzhaf: +-1 / 2^(|S|-1)).  A feature met at several path positions is one
 // variable (cubes are sets); its value sits at its first position.
 __global__ void k_tables(int D, int metric, const uint32_t *__restrict__ keys, float *__restrict__ t32,
-                         double *__restrict__ t64, float *__restrict__ t32t) {
+                         double *__restrict__ t64) {
     const int g = blockIdx.y;
     const int K = 1 << D, N = D << D;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -57,17 +57,15 @@ __global__ void k_tables(int D, int metric, const uint32_t *__restrict__ keys, f
         }
         t32[rowbase + ((size_t)k << D) + pc] = (float)v;
         if (t64) t64[rowbase + ((size_t)k << D) + pc] = v;
-        // K-major copy [g][column][p_b] for the tensor-core contraction
-        if (t32t) t32t[((size_t)g * N + ((size_t)k << D) + pc) * K + pb] = (float)v;
     }
 }
 
-cudaError_t launch_tables(int D, int metric, const uint32_t *sig_keys, int G, float *t32, double *t64, float *t32t,
+cudaError_t launch_tables(int D, int metric, const uint32_t *sig_keys, int G, float *t32, double *t64,
                           cudaStream_t st) {
     if (G == 0) return cudaSuccess;
     const int total = 1 << (2 * D);
     dim3 grid((total + 255) / 256, G);
-    k_tables<<<grid, 256, 0, st>>>(D, metric, sig_keys, t32, t64, t32t);
+    k_tables<<<grid, 256, 0, st>>>(D, metric, sig_keys, t32, t64);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -144,10 +142,11 @@ cudaError_t launch_contract_fp32(int D, const float *A, const float *scale, cons
 // the subtree root r the entry fixes the leaf's consumer pattern p; the slot vector
 // collects sum over leaves of S[leaf][k][p] per path position k: positions above r
 // (slots 0..D-3) and r itself (slot D-2) from all four leaves, the left child of r
-// (slot D-1) from leaves 0-1 and the right child (slot D) from leaves 2-3.
+// (slot D-1) from leaves 0-1 and the right child (slot D) from leaves 2-3.  The vector
+// of entry e is stored at line_pos(e) of the subtree's line map.
 __global__ void k_fold(int D, const float *__restrict__ S, const int32_t *__restrict__ leaf_row, int T,
-                       float *__restrict__ sfold) {
-    const int NS = 1 << (D - 2), E = 1 << (D + 1), K = 1 << D, NL = 1 << D, N = D << D;
+                       const uint32_t *__restrict__ lines, float *__restrict__ sfold) {
+    const int NS = 1 << (D - 2), E = 1 << (D + 1), NL = 1 << D, N = D << D;
     const int SP = (D + 1) <= 4 ? 4 : ((D + 1) <= 8 ? 8 : 12);
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)T * NS * E) return;
@@ -170,14 +169,67 @@ __global__ void k_fold(int D, const float *__restrict__ S, const int32_t *__rest
         for (int k = 0; k <= D - 2; ++k) out[k] += __ldg(Sr + ((size_t)k << D) + p);
         out[(j < 2) ? D - 1 : D] += __ldg(Sr + ((size_t)(D - 1) << D) + p);
     }
-    (void)K;
-    float4 *dst = reinterpret_cast<float4 *>(sfold + idx * SP);
+    const uint32_t map = (__ldg(lines + (size_t)t * lines_words(D) + (s >> 2)) >> (8 * (s & 3))) & 0xFFu;
+    const int64_t at = ((int64_t)t * NS + s) * E + line_pos((uint32_t)e, map);
+    float4 *dst = reinterpret_cast<float4 *>(sfold + at * SP);
     for (int k = 0; k < SP; k += 4) dst[k / 4] = make_float4(out[k], out[k + 1], out[k + 2], out[k + 3]);
 }
 
-cudaError_t launch_fold(int D, const float *S, const int32_t *leaf_row, int T, float *sfold, cudaStream_t st) {
+cudaError_t launch_fold(int D, const float *S, const int32_t *leaf_row, int T, const uint32_t *lines, float *sfold,
+                        cudaStream_t st) {
     const int64_t total = (int64_t)T << (D - 2 + D + 1);
-    k_fold<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(D, S, leaf_row, T, sfold);
+    k_fold<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(D, S, leaf_row, T, lines, sfold);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// One thread per (tree, word of line maps): for each of its (up to) four subtrees, the
+// background frequency of every entry bit b (the share of rows with bit b set); the two
+// bits nearest one half become b0 < b1.  Ties keep the lower bit; a subtree no row
+// reaches keeps the identity.
+__global__ void k_line_maps(int D, const uint32_t *__restrict__ hist, int T, uint32_t *__restrict__ lines) {
+    const int NS = 1 << (D - 2), E = 1 << (D + 1), W = lines_words(D);
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)T * W) return;
+    const int t = (int)(idx / W), w = (int)(idx % W);
+    uint32_t word = 0;
+    for (int q = 0; q < 4; ++q) {
+        const int s = 4 * w + q;
+        uint32_t map = 0x10u;
+        if (s < NS && hist) {
+            const uint32_t *h = hist + ((size_t)t * NS + s) * E;
+            double total = 0.0, ones[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int e = 0; e < E; ++e) {
+                const double c = (double)__ldg(h + e);
+                total += c;
+                for (int b = 0; b <= D; ++b)
+                    if ((e >> b) & 1) ones[b] += c;
+            }
+            if (total > 0.0) {
+                int best0 = 0, best1 = 1;
+                double u0 = -1.0, u1 = -1.0;  // u0 >= u1: the two largest uncertainties
+                for (int b = 0; b <= D; ++b) {
+                    const double pb = ones[b] / total, u = pb < 1.0 - pb ? pb : 1.0 - pb;
+                    if (u > u0) {
+                        u1 = u0; best1 = best0;
+                        u0 = u; best0 = b;
+                    } else if (u > u1) {
+                        u1 = u; best1 = b;
+                    }
+                }
+                const int b0 = best0 < best1 ? best0 : best1, b1 = best0 < best1 ? best1 : best0;
+                map = ((uint32_t)b1 << 4) | (uint32_t)b0;
+            }
+        }
+        word |= map << (8 * q);
+    }
+    lines[idx] = word;
+}
+
+cudaError_t launch_line_maps(int D, const uint32_t *hist, int T, uint32_t *lines, cudaStream_t st) {
+    const int64_t total = (int64_t)T * lines_words(D);
+    if (total == 0) return cudaSuccess;
+    k_line_maps<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(D, hist, T, lines);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -109,13 +109,70 @@ __device__ __forceinline__ void load_offsets8(const int *p, int (&o)[8]) {
     o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
 }
 
-// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble.  ENC:
-// the tile's decision codes are computed here from C; otherwise they are copied from
-// codes, the code blocks of all n rows (padded to a multiple of TC rows).
-template <int D, int TC, bool ENC>
+// Decision codes (tree_layout.h) of the tile's rows, written into the code tile sx in
+// 32-row code blocks.  The rows are first staged in the phi region (free until the tree
+// loop), TC rows of FS floats (FS = F rounded up to odd, so that the lanes of a warp,
+// one row each, read different banks); then warp w encodes code block w, lane = row,
+// one binary search per code column, sixteen columns in flight so their dependent
+// threshold loads overlap.  A row past n gets code 0 (its phi is never written).
+template <int TC>
+__device__ __forceinline__ void encode_tile(const float *__restrict__ C, int64_t n, int64_t ldc, int64_t c0,
+                                            const TreeArrays &ta, int F, float *stage, unsigned char *sx, int tid) {
+    constexpr int IL = 16;  // searches in flight per thread: their threshold loads are mostly L2 round trips
+    const int FS = F | 1;
+    const int rows = (int)min((int64_t)TC, n - c0);
+    for (int r = tid / 32; r < TC; r += TC / 32) {  // one warp per row at a time: coalesced
+        const float *src = C + (c0 + r) * ldc;
+        for (int f = tid & 31; f < F; f += 32) stage[r * FS + f] = r < rows ? __ldg(src + f) : 0.0f;
+    }
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5, row = warp * 32 + lane;
+    const bool valid = row < rows;
+    const float *xr = stage + row * FS;
+    const int ncol = ta.n_cols, cb = ta.code_bytes;
+    unsigned char *dst = sx + (size_t)warp * 32 * ncol * cb;
+    const int4 *cols = reinterpret_cast<const int4 *>(ta.cols);
+    if (cb == 1) {
+        // one-byte columns hold 255 thresholds padded with NaN (never <= x): a search from
+        // the column's top power of two needs no bound checks; NaN x gets the count
+        for (int cc = 0; cc < ncol; cc += IL) {
+            float x[IL];
+            int pos[IL], top[IL], first[IL];
+#pragma unroll
+            for (int j = 0; j < IL; ++j) {
+                const int4 cv = cc + j < ncol ? __ldg(cols + cc + j) : make_int4(0, 0, 0, 0);
+                x[j] = xr[cv.x];
+                first[j] = cv.y;
+                top[j] = cv.w;
+                pos[j] = x[j] != x[j] ? -cv.z - 1 : 0;  // NaN: the count, kept out of the search
+            }
+#pragma unroll
+            for (int step = 128; step > 0; step >>= 1) {
+#pragma unroll
+                for (int j = 0; j < IL; ++j)
+                    if (step <= top[j] && pos[j] >= 0)
+                        pos[j] += __ldg(ta.col_thr + first[j] + pos[j] + step - 1) <= x[j] ? step : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < IL; ++j)
+                if (cc + j < ncol)
+                    dst[(cc + j) * 32 + lane] = (unsigned char)(!valid ? 0 : (pos[j] < 0 ? -pos[j] - 1 : pos[j]));
+        }
+    } else {
+        for (int c = 0; c < ncol; ++c) {
+            const int4 cv = __ldg(cols + c);
+            const int code = valid ? decision_code(xr[cv.x], ta.col_thr + cv.y, CodeCol{cv.x, cv.y, cv.z, cv.w}) : 0;
+            reinterpret_cast<uint16_t *>(dst)[c * 32 + lane] = (uint16_t)code;
+        }
+    }
+    __syncthreads();
+}
+
+// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble: the
+// rows' decision codes are computed here from C (encode_tile), then every tree.
+template <int D, int TC>
 __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float *__restrict__ C, int64_t n,
-                                             int64_t ldc, const unsigned char *__restrict__ codes,
-                                             float *__restrict__ phi, int64_t ldp, int64_t c0,
+                                             int64_t ldc, float *__restrict__ phi, int64_t ldp, int64_t c0,
                                              unsigned char *smem_raw) {
     using S = Shape<D>;
     using X = ExplainCfg<D>;
@@ -127,7 +184,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
     const int F = job.F, T = job.T;
     const TreeArrays &ta = job.ta;
     const float *__restrict__ sfold = job.sfold;
-    const int ncol = ta.n_cols, cb = ta.code_bytes, xb = ncol * cb;
+    const int cb = ta.code_bytes, xb = ta.n_cols * cb;
     const ExLayout<D> L(F, xb, TC);
     unsigned char *sx = smem_raw;
     float *sp = reinterpret_cast<float *>(smem_raw + L.x);
@@ -135,49 +192,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
     int4 *srec = reinterpret_cast<int4 *>(smem_raw + L.x + L.p + L.meta);
     int *sfl = reinterpret_cast<int *>(smem_raw + L.x + L.p + L.meta + L.rec);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if constexpr (!ENC) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(codes + c0 * xb);
-        for (int i = tid; i < TC * xb / 16; i += TC) reinterpret_cast<uint4 *>(sx)[i] = __ldg(src + i);
-    } else {
-        // decision codes of the tile's rows (tree_layout.h), in 32-row code blocks.  Thread
-        // tid encodes elements tid + TC * k (row-major over the tile, so a warp reads
-        // consecutive features of a row), eight binary searches in lockstep so that their
-        // threshold loads overlap.
-        for (int k0 = 0; k0 < ncol; k0 += 8) {
-            float x[8];
-            int pos[8], r[8], c[8];
-            CodeCol col[8];
-    #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int e = tid + TC * (k0 + j);
-                r[j] = e / ncol;
-                c[j] = e - r[j] * ncol;
-                const bool act = k0 + j < ncol;
-                const int4 cv = act ? __ldg(reinterpret_cast<const int4 *>(ta.cols) + c[j]) : make_int4(0, 0, 0, 0);
-                col[j] = CodeCol{cv.x, cv.y, cv.z, cv.w};
-                x[j] = (act && c0 + r[j] < n) ? __ldg(C + (c0 + r[j]) * ldc + cv.x) : 0.0f;
-                pos[j] = 0;
-            }
-            for (int step = cb == 1 ? 128 : 32768; step > 0; step >>= 1) {
-    #pragma unroll
-                for (int j = 0; j < 8; ++j) {  // branch-free: an out-of-range probe reads the first threshold
-                    const bool in = pos[j] + step <= col[j].count;
-                    const float u = __ldg(ta.col_thr + col[j].first + (in ? pos[j] + step - 1 : 0));
-                    pos[j] += (in && u <= x[j]) ? step : 0;
-                }
-            }
-    #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (k0 + j >= ncol) break;
-                const int code = x[j] != x[j] ? col[j].count : pos[j];
-                unsigned char *dst = sx + (size_t)(r[j] >> 5) * 32 * xb + ((size_t)c[j] * 32 + (r[j] & 31)) * cb;
-                if (cb == 1)
-                    *dst = (unsigned char)code;
-                else
-                    *reinterpret_cast<uint16_t *>(dst) = (uint16_t)code;
-            }
-        }
-    }
+    encode_tile<TC>(C, n, ldc, c0, ta, F, sp, sx, tid);
     for (int i = tid; i < (F + 1) * XS; i += TC) sp[i] = 0.0f;
     float *myphi = sp + tid;
     const CodeReader xr(sx + (size_t)warp * 32 * xb, lane, cb);
@@ -205,6 +220,14 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
             const uint64_t lv = mt.live;
             const uint32_t fok = mt.flush, real = mt.real;
             const float4 *tf = reinterpret_cast<const float4 *>(sfold + (size_t)t * S::NS * S::E * S::SP);
+            // the tree's line maps (launch.h), one byte per bottom subtree
+            constexpr int LW = lines_words(D);
+            uint32_t lmap[LW];
+#pragma unroll
+            for (int w = 0; w < LW; w += 4) {
+                const uint4 v4 = __ldg(reinterpret_cast<const uint4 *>(job.lines + (size_t)t * LW) + w / 4);
+                lmap[w] = v4.x; lmap[w + 1] = v4.y; lmap[w + 2] = v4.z; lmap[w + 3] = v4.w;
+            }
             float acc[NA];
 #pragma unroll
             for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
@@ -216,7 +239,8 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
 #pragma unroll
                 for (int j = 0; j < GS; ++j) {
                     const uint32_t lj = (uint32_t)(lv >> (s0 + j)) & 1u;
-                    const float4 *src = tf + ((size_t)(s0 + j) * S::E + ent[s0 + j]) * Q;
+                    const uint32_t map = (lmap[(s0 + j) >> 2] >> (8 * ((s0 + j) & 3))) & 0xFFu;
+                    const float4 *src = tf + ((size_t)(s0 + j) * S::E + line_pos(ent[s0 + j], map)) * Q;
 #pragma unroll
                     for (int k = 0; k < Q; ++k) v[j][k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     if (Q == 2) {
@@ -290,10 +314,10 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
 // 1 block per SM is enough (shared memory limits residency anyway): the register
 // budget then covers a whole gather group in flight.
 template <int D, int TC>
-__global__ void __launch_bounds__(TC, 1) k_explain(const unsigned char *__restrict__ codes, int64_t n,
+__global__ void __launch_bounds__(TC, 1) k_explain(const float *__restrict__ C, int64_t n, int64_t ldc,
                                                    ExplainJob job, float *__restrict__ phi, int64_t ldp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    explain_tile<D, TC, false>(job, nullptr, n, 0, codes, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
+    explain_tile<D, TC>(job, C, n, ldc, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
 }
 
 // Persistent form over a ragged batch: work item i is (job, request, first row).  Blocks
@@ -318,13 +342,13 @@ __global__ void __launch_bounds__(TC, 1) k_explain_batch(const ExplainJob *__res
         const ExplainJob job = jobs[it.x];
         const BatchRequest rq = reqs[it.y];
         const int64_t c0 = ((int64_t)it.z << 31) | (uint32_t)it.w;
-        explain_tile<D, TC, true>(job, rq.C, rq.n, rq.ldc, nullptr, rq.phi, rq.ldp, c0, smem_raw);
+        explain_tile<D, TC>(job, rq.C, rq.n, rq.ldc, rq.phi, rq.ldp, c0, smem_raw);
         __syncthreads();
     }
 }
 
 template <int D, int TC>
-cudaError_t explain_t(const unsigned char *codes, int64_t n, const ExplainJob &job, float *phi, int64_t ldp,
+cudaError_t explain_t(const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi, int64_t ldp,
                       const DevInfo &dev, cudaStream_t st) {
     const size_t smem = ExLayout<D>(job.F, job.ta.n_cols * job.ta.code_bytes, TC).total;
     if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
@@ -332,7 +356,7 @@ cudaError_t explain_t(const unsigned char *codes, int64_t n, const ExplainJob &j
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     const int64_t blocks = (n + TC - 1) / TC;
-    kern<<<(unsigned)blocks, TC, smem, st>>>(codes, n, job, phi, ldp);
+    kern<<<(unsigned)blocks, TC, smem, st>>>(C, n, ldc, job, phi, ldp);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -359,7 +383,7 @@ cudaError_t batch_t(const ExplainJob *jobs, const BatchRequest *reqs, const int4
 // Explicit instantiation of the kernels of one (depth, tile rows) pair; each pair is
 // compiled in one of the k_explain_d*.cu translation units.
 #define WDF_EXPLAIN_TILE(d, tc, spec)                                                                            \
-    spec template cudaError_t explain_t<d, tc>(const unsigned char *, int64_t, const ExplainJob &, float *,       \
+    spec template cudaError_t explain_t<d, tc>(const float *, int64_t, int64_t, const ExplainJob &, float *,     \
                                                int64_t, const DevInfo &, cudaStream_t);                          \
     spec template cudaError_t batch_t<d, tc>(const ExplainJob *, const BatchRequest *, const int4 *, int *, int,  \
                                              int, int, const DevInfo &, cudaStream_t);

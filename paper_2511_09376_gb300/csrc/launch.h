@@ -25,9 +25,29 @@ struct TreeArrays {
 // Everything the consumer kernel needs about one ensemble.
 struct ExplainJob {
     TreeArrays ta;
-    const float *sfold;  // folded slot vectors [T][NS][2^(D+1)][SP]
+    const float *sfold;     // folded slot vectors [T][NS][2^(D+1)][SP], entry e at line_pos(e)
+    const uint32_t *lines;  // per tree lines_words(D) words: byte s = line map of subtree s
     int T, F;
 };
+
+// Where the consumer gathers land.  A warp's 32-byte gathers of one bottom subtree are
+// served a quarter warp at a time, one L1 wavefront per distinct 128-byte line, and a
+// line holds four consecutive entries.  Entries are formed from D + 1 decision bits;
+// the two bits whose background frequency is closest to one half are moved to the two
+// lowest positions (within a line), so the rows of a quarter warp, which mostly agree on
+// the more certain decisions, land in fewer lines.  The map of subtree s is one byte,
+// (b1 << 4) | b0 with b0 < b1: swap bit 0 with bit b0, then bit 1 with bit b1 (a
+// permutation of the entries; 0x10 is the identity).
+__host__ __device__ __forceinline__ uint32_t line_pos(uint32_t e, uint32_t map) {
+    const uint32_t b0 = map & 15u, b1 = map >> 4;
+    uint32_t x = (e ^ (e >> b0)) & 1u;
+    e ^= x | (x << b0);
+    x = ((e >> 1) ^ (e >> b1)) & 1u;
+    return e ^ ((x << 1) | (x << b1));
+}
+// 32-bit words of line maps per tree: one byte per bottom subtree, at least four words
+// so that a tree's maps are whole 16-byte loads.
+__host__ __device__ constexpr int lines_words(int D) { return (1 << (D - 2)) / 4 < 4 ? 4 : (1 << (D - 2)) / 4; }
 
 // One request of a ragged batch: n consumer rows at C (row stride ldc), phi out.
 struct BatchRequest {
@@ -52,9 +72,18 @@ constexpr int kBgMaxTileRows = 512;
 // blocks (wdf_device.cuh); rows up to rows_pad (a multiple of 32) get code 0.
 cudaError_t launch_encode_codes(const float *X, int64_t rows, int64_t ldx, const TreeArrays &ta, int64_t rows_pad,
                                 unsigned char *codes, cudaStream_t st);
+// With ov, chunks alternate between codes and ov->codes1 and are encoded on ov->side, so
+// the encode of chunk k + 1 overlaps the count of chunk k (events order each buffer's
+// encode after its previous count and each count after its encode); st still ends
+// after all of it.
+struct BgOverlap {
+    unsigned char *codes1;
+    cudaStream_t side;
+    cudaEvent_t enc[2], cnt[2];
+};
 cudaError_t launch_bg_hist(int D, const float *B, int64_t m, int64_t ldb, const TreeArrays &ta, int T,
                            unsigned char *codes, int64_t code_rows, uint32_t *hist, const DevInfo &dev,
-                           cudaStream_t st);
+                           cudaStream_t st, const BgOverlap *ov = nullptr);
 
 // Per-leaf pattern counts vc[row][p] (u32, 2^D per row) of the live leaves, marginals of
 // the joint entry counts; A (nullable) receives them as FP32.
@@ -66,9 +95,8 @@ cudaError_t launch_leaf_counts(int D, const uint32_t *hist, const int32_t *group
 cudaError_t launch_pd_freq(int D, const double *ratio, int n_live, float *A, cudaStream_t st);
 
 // Step 2: FP64 pattern-pair tables of G path signatures; t32 (and t64 when non-null)
-// laid out [G][2^D][D * 2^D]; t32t (when non-null) the K-major copy [G][D * 2^D][2^D].
-// metric 0: Shapley values, 1: Banzhaf values.
-cudaError_t launch_tables(int D, int metric, const uint32_t *sig_keys, int G, float *t32, double *t64, float *t32t,
+// laid out [G][2^D][D * 2^D].  metric 0: Shapley values, 1: Banzhaf values.
+cudaError_t launch_tables(int D, int metric, const uint32_t *sig_keys, int G, float *t32, double *t64,
                           cudaStream_t st);
 
 // Step 3 on CUDA cores: S[row][k * 2^D + p_c] = scale[row] * sum_p A[row][p] *
@@ -80,15 +108,33 @@ cudaError_t launch_contract_fp32(int D, const float *A, const float *scale, cons
 
 // Step 3 on the tensor cores (tcgen05, TMEM accumulators): the same S as
 // launch_contract_fp32 from split-precision operands: mode 0 = TF32 hi+lo, 1 = BF16
-// hi+lo (three products each), 2 = BF16 hi+mid+lo (six products).
-// tiles: (group, row0, row_end, 0) work items of up to 128 rows; t32t the K-major tables.
-// err is set to 1 if a bounded wait expired.
+// hi+lo (three products each), 2 = BF16 hi+mid+lo (six products).  The operands are
+// split once into the core-matrix stages the MMAs read: B (the tables, per signature) by
+// launch_pack_b into bpk (contract_tc_b_bytes), A (the frequencies) by the contraction
+// itself into apk (contract_tc_a_bytes: room for any mode).  tiles: (group, row0,
+// row_end, 0) work items of up to 128 rows.  err is set to 1 if a bounded wait expired.
+struct TcGeom {
+    int NT, NB, nk, ring, np;  // N per CTA, column blocks, K steps, ring stages, operand parts
+    uint32_t a_stage, b_stage;  // bytes of one stage of A and of B
+    size_t smem;
+};
+TcGeom tc_geom(int D, int mode);
+size_t contract_tc_a_bytes(int D, int n_tiles);
+size_t contract_tc_b_bytes(int D, int mode, int G);
+cudaError_t launch_pack_b(int D, int mode, const float *t32, int G, unsigned char *bpk, cudaStream_t st);
 cudaError_t launch_contract_tc(int D, int mode, const float *A, const float *scale, const int4 *tiles, int n_tiles,
-                               const float *t32t, float *S, int *err, cudaStream_t st);
+                               unsigned char *apk, const unsigned char *bpk, float *S, int *err, cudaStream_t st);
+// Test hook: poll limit of the first mbarrier wait of every CTA of later launches (0
+// restores the normal limit).
+void set_contract_first_wait_limit(uint32_t polls);
 
 // Folds the per-leaf S rows of every bottom subtree into per-entry slot vectors
 // sfold[T][NS][2^(D+1)][SP] (see wdf_internal.h).
-cudaError_t launch_fold(int D, const float *S, const int32_t *leaf_row, int T, float *sfold, cudaStream_t st);
+cudaError_t launch_fold(int D, const float *S, const int32_t *leaf_row, int T, const uint32_t *lines, float *sfold,
+                        cudaStream_t st);
+// Line maps of every bottom subtree from the joint background counts hist (hist null:
+// the identity map, used for the path-dependent frequencies).
+cudaError_t launch_line_maps(int D, const uint32_t *hist, int T, uint32_t *lines, cudaStream_t st);
 
 // scale[row] = w[row] / m.
 cudaError_t launch_scale(const double *w, int n_live, int64_t m, float *scale, cudaStream_t st);
@@ -130,8 +176,9 @@ cudaError_t launch_explain_iv(int D, const float *C, int64_t n, int64_t ldc, int
                               int64_t ldo, const DevInfo &dev, cudaStream_t st);
 
 // FP64 column means of |phi| and phi: partial sums per row block, then a fixed-order
-// final sum.  partial holds n_blocks * F * 2 doubles.
-int global_attr_blocks(int64_t n);
+// final sum.  partial holds global_attr_partial_doubles(n, F) doubles.
+int64_t global_attr_blocks(int64_t n);
+int64_t global_attr_partial_doubles(int64_t n, int F);
 cudaError_t launch_global_attr(const float *phi, int64_t n, int64_t ldp, int F, double *partial,
                                double *mean_abs, double *mean, cudaStream_t st);
 

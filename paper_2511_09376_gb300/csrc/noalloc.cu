@@ -49,8 +49,9 @@ extern "C" wdf_status wdf_global_attribution_noalloc(int32_t device, const float
     if (n < 0 || n_features < 1 || ldphi < n_features)
         return fail(WDF_EINVAL, "bad sizes: need n >= 0, n_features >= 1, ldphi >= n_features");
     if (device < 0 || device >= kMaxDevices) return fail(WDF_EINVAL, "device index out of range");
-    const size_t need = (size_t)wdf::global_attr_blocks(n) * (size_t)n_features * 2;
-    if (need > kNoAllocScratchDoubles)
+    // in 64-bit arithmetic before any narrowing, so that no size wraps past the check
+    const int64_t need = wdf::global_attr_partial_doubles(n, n_features);
+    if (need > (int64_t)kNoAllocScratchDoubles)
         return fail(WDF_EINVAL, "n * n_features too large for the fixed scratch: needs " + std::to_string(need) +
                                     " doubles of partial sums, the library holds " +
                                     std::to_string(kNoAllocScratchDoubles) +

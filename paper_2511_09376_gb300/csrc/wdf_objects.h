@@ -32,15 +32,18 @@ struct wdf_ensemble {
     wdf::TreeMeta *d_meta = nullptr;
     wdf::CodeCol *d_cols = nullptr;
     float *d_col_thr = nullptr;
-    // tensor-core contraction: K-major tables, 128-row tiles, wait-expiry flag
-    float *d_t32t = nullptr;
+    // tensor-core contraction: split operand stages (A for any mode, B for bpk_mode),
+    // 128-row tiles, wait-expiry flag
+    unsigned char *d_apk = nullptr;
+    unsigned char *d_bpk = nullptr;
+    int bpk_mode = -1;
     int4 *d_tiles128 = nullptr;
     int n_tiles128 = 0;
     int *d_err = nullptr;
     wdf::TreeArrays arrays() const {
         return wdf::TreeArrays{d_nodes, d_rec, d_meta, d_cols, d_col_thr, (int)pk.cols.size(), pk.code_bytes};
     }
-    wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, pk.T, pk.F}; }
+    wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, d_lines, pk.T, pk.F}; }
     // background state (set_background)
     int has_bg = 0;
     int64_t m = 0;
@@ -49,6 +52,7 @@ struct wdf_ensemble {
     float *d_scale = nullptr;
     float *d_S = nullptr;
     float *d_sfold = nullptr;
+    uint32_t *d_lines = nullptr;  // line maps of the folded vectors (launch.h)
     double *d_base = nullptr;
     // staging for host-memory calls: two buffers per direction, one per internal stream
     float *d_stage_in[2] = {nullptr, nullptr};
@@ -59,5 +63,6 @@ struct wdf_ensemble {
     int64_t code_rows = 0;
     cudaStream_t ist[2] = {nullptr, nullptr};
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    cudaEvent_t ev_enc[2] = {nullptr, nullptr}, ev_cnt[2] = {nullptr, nullptr};  // encode / count overlap
 };
 
