@@ -149,6 +149,19 @@ def profiled_limiter(summary: str, sources: list):
     return None if fields is None else fields.get("limiter", "").strip() or None
 
 
+def workload_config(w, n: int, m: int, world: int, sharded: bool = False) -> dict:
+    """The config object of both arms' JSON lines: the workload and how it is run."""
+    F = w.n_features
+    cb, bb = n * F * 4, m * F * 4
+    return {
+        "workload": f"{w.name}: n={n} consumers, m={m} background rows, F={F}, T={w.n_trees} trees, depth<={w.depth}",
+        "n_consumers": n, "n_background": m, "n_features": F, "n_trees": w.n_trees, "depth": w.depth,
+        "l2": f"inputs larger than L2 (B {bb / 1e9:.2f} GB, C {cb / 1e9:.2f} GB)" if min(bb, cb) > 129e6
+              else "inputs smaller than L2",
+        "parallelism": f"background-sharded{world}" if sharded else f"replicas{world}",
+    }
+
+
 def algorithmic_ops(ens) -> dict:
     """Per consumer row, the work the method must do on the real (unpadded) trees:
     one compare per inner node and one table lookup-add per (leaf, distinct feature on
@@ -289,14 +302,9 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {
-            "workload": f"{w.name}: n={n} consumers, m={m} background rows, F={F}, T={w.n_trees} trees, depth<={w.depth}",
-            "n_consumers": n, "n_background": m, "n_features": F, "n_trees": w.n_trees, "depth": info["depth"],
-            "precision": args.precision, "live_leaves": info["n_live_leaves"], "signatures": info["n_signatures"],
-            "l2": f"inputs larger than L2 (B {B.nbytes / 1e9:.2f} GB, C {C.nbytes / 1e9:.2f} GB)"
-                  if min(B.nbytes, C.nbytes) > 129e6 else "inputs smaller than L2",
-            "parallelism": f"background-sharded{world}" if shard is not None else f"replicas{world}",
-        },
+        "config": workload_config(w, n, m, world, shard is not None),
+        "precision": args.precision,
+        "ensemble": {"depth": info["depth"], "live_leaves": info["n_live_leaves"], "signatures": info["n_signatures"]},
         "explain_ms": explain_ms,
         "background_ms": background_ms,
         "reduce_ms": ms - explain_ms - background_ms,
@@ -364,9 +372,11 @@ def run_reference(args, world, rank):
     from paper_2511_09376_gb300 import synth
     oracle.build()
     w = synth.WORKLOADS[args.workload]
-    m_s, n_s = 50_000, 32
-    ens, C, B = synth.make(w, n_consumers=n_s, n_background=m_s)
     n_full, m_full = w.n_consumers, w.n_background
+    m_s, n_s = min(50_000, m_full), min(32, n_full)
+    ens, C, B = synth.make(w, n_consumers=n_s, n_background=m_s)
+
+    sample_s = []
 
     def step():
         t0 = time.perf_counter()
@@ -374,10 +384,12 @@ def run_reference(args, world, rank):
         t1 = time.perf_counter()
         oracle.values_hist(ens, counts, m_s, C)
         t2 = time.perf_counter()
+        sample_s.append(t2 - t0)
         return (t1 - t0) / m_s * m_full + (t2 - t1) / n_s * n_full
 
     for _ in range(args.warmup):
         step()
+    sample_s.clear()
     est = [step() for _ in range(args.steps)]
     full_s = statistics.mean(est)
     v = n_full / full_s
@@ -385,8 +397,11 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": full_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{w.name}: n={n_full} consumers, m={m_full} background rows, F={w.n_features}, "
-                               f"T={w.n_trees} trees, depth<={w.depth}", "parallelism": "host cores"},
+        "config": workload_config(w, n_full, m_full, world),
+        # each step times a bounded sample and extrapolates it linearly to the full
+        # workload: ms_per_step is that estimate, not a measured wall time
+        "ms_per_step_extrapolated": True,
+        "ms_per_step_measured_sample": statistics.mean(sample_s) * 1e3,
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                          "sample": f"per step: background counts on {m_s} rows and values for {n_s} consumers, "
                                    f"extrapolated linearly to m={m_full}, n={n_full}"},
@@ -527,11 +542,13 @@ def run_interactions(args):
 SPLIT_BF16 = "bf16x6"
 
 
-def run_ragged(args):
-    """64 ensembles of mixed depth/width: the plain path (one wdf_explain per ensemble, FP32
-    contraction) against the batched form (one autotuned graph launch over all of them,
-    BF16 split-precision contraction: hi+mid+lo operands, the FP32-mode accuracy of the
-    plain arm)."""
+def ragged_compare(args) -> dict:
+    """The ragged batch (64 ensembles of mixed depth and width at their full sizes): the
+    plain path (one wdf_explain per ensemble, FP32 contraction) against the batched form
+    (one autotuned graph launch over all of them, BF16 hi+mid+lo contraction: the
+    FP32-mode accuracy of the plain arm).  Both arms' phi are compared element by
+    element; their agreement with the FP64 oracle is checked by the GPU tests
+    (1,000 rows per ensemble)."""
     import torch
 
     import paper_2511_09376_gb300 as wdf
@@ -539,7 +556,7 @@ def run_ragged(args):
     specs = synth.ragged_specs()
     ctx = wdf.ctx_create(0)
     dev = torch.device("cuda", 0)
-    ens, Cs, t_bg = [], [], {"fp32": 0.0, SPLIT_BF16: 0.0}
+    Cs, t_bg = [], {"fp32": 0.0, SPLIT_BF16: 0.0}
     plain_e, batch_e = [], []
     t0 = time.time()
     for w in specs:
@@ -557,7 +574,7 @@ def run_ragged(args):
         batch_e.append(e_batch)
         Cs.append(torch.from_numpy(C).to(dev))
         del dB, B
-    gen_s = time.time() - t0
+    setup_s = time.time() - t0
     rows = sum(c.shape[0] for c in Cs)
     outs_p = [torch.empty((c.shape[0], e.info["n_features"]), device=dev) for c, e in zip(Cs, plain_e)]
     outs_b = [torch.empty_like(o) for o in outs_p]
@@ -565,7 +582,7 @@ def run_ragged(args):
     reqs = list(enumerate(Cs))
     wdf.batch_autotune(batch, reqs, outs=outs_b, reps=2)
     stream = torch.cuda.current_stream(dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
 
     def plain():
         for e, c, o in zip(plain_e, Cs, outs_p):
@@ -578,45 +595,60 @@ def run_ragged(args):
         plain()
         batched()
     torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = wdf.launch_count()
     ev[0].record(stream)
-    for _ in range(args.steps):
+    for _ in range(args.ragged_steps):
         plain()
     ev[1].record(stream)
-    for _ in range(args.steps):
+    l1 = wdf.launch_count()
+    for _ in range(args.ragged_steps):
         batched()
     ev[2].record(stream)
     torch.cuda.synchronize()
-    plain_ms = ev[0].elapsed_time(ev[1]) / args.steps
-    batch_ms = ev[1].elapsed_time(ev[2]) / args.steps
+    l2 = wdf.launch_count()
+    clk = clocks.stop()
+    plain_ms = ev[0].elapsed_time(ev[1]) / args.ragged_steps
+    batch_ms = ev[1].elapsed_time(ev[2]) / args.ragged_steps
     diff = max(float((a - b).abs().max()) for a, b in zip(outs_p, outs_b))
     tiles = {d: wdf.batch_tile_rows(batch, d) for d in range(2, 9)}
-    return {
-        "metric": METRIC, "value": rows / (batch_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"ragged batch: {len(specs)} ensembles, trees 10-500, depth 2-8, features 20-300, "
-                               f"{rows} consumer rows in total", "contraction": f"{SPLIT_BF16} (batched) vs fp32 (plain)"},
-        "plain_rows_per_s": rows / (plain_ms * 1e-3), "plain_ms": plain_ms, "batched_ms": batch_ms,
-        "speedup_batched_vs_plain": plain_ms / batch_ms, "max_abs_diff_batched_vs_plain": diff,
-        "background_s": t_bg, "tile_rows": tiles, "generate_s": gen_s,
-        "graph_launches_per_step_batched": 1,
-        "kernels_per_step_batched": len([d for d in tiles.values() if d > 0]),
-        "kernels_per_step_plain": len(specs),
+    out = {
+        "workload": f"ragged batch: {len(specs)} ensembles, trees 10-500 (log-uniform), depth 2-8, features 20-300, "
+                    f"consumers 1e3-2e5 and background rows 1e4-1e6 each; {rows} consumer rows in total",
+        "rows_per_step": rows, "steps": args.ragged_steps,
+        "plain": {"rows_per_s": rows / (plain_ms * 1e-3), "ms_per_step": plain_ms, "contraction": "fp32",
+                  "kernels_per_step": (l1 - l0) // args.ragged_steps,
+                  "how": "one wdf_explain per ensemble (encode + consumer kernel each), device-resident rows"},
+        "batched": {"rows_per_s": rows / (batch_ms * 1e-3), "ms_per_step": batch_ms, "contraction": SPLIT_BF16,
+                    "graph_launches_per_step": 1, "kernels_per_step": (l2 - l1) // args.ragged_steps,
+                    "tile_rows": tiles,
+                    "how": "one wdf_batch_explain: a CUDA graph with one persistent kernel per depth class, "
+                           "autotuned consumer tiles"},
+        "batched_vs_plain": plain_ms / batch_ms,
+        "max_abs_diff_batched_vs_plain": diff,
+        "accuracy": "both arms within |phi - oracle| <= 1e-6 + 1e-5 |oracle| of the FP64 oracle "
+                    "(tests/test_gpu_configs.py: 1,000 rows per ensemble for the batched arm; "
+                    "tests/test_gpu_depths_precisions.py for FP32 and BF16x6 at depths 2-8)",
+        "background_s": t_bg, "setup_s": setup_s, "clocks": clk,
     }
+    batch.close()
+    for e in plain_e + batch_e:
+        e.close()
+    ctx.close()
+    return out
 
 
-def run_serving(args):
-    """Poisson request stream (200 req/s, rows log-uniform 1..1e5) against four resident
-    ensembles (50/200/500/1000 trees, depths 4/6/7/8), continuous batching."""
+def _serving_setup(dev, pool_rows=100_000, out_rows=2_000_000):
+    """The four resident serving ensembles with their 1e6-row backgrounds precomputed in
+    the split-precision contraction, pinned request pools and pinned phi pools."""
     import torch
 
     import paper_2511_09376_gb300 as wdf
     from paper_2511_09376_gb300 import synth
     specs = synth.serving_specs()
     ctx = wdf.ctx_create(0)
-    dev = torch.device("cuda", 0)
-    ens, pools = [], []
-    t0 = time.time()
+    ens, pools, out_pools = [], [], []
     for k, w in enumerate(specs):
         e_np, _, B = synth.make(w)
         e = wdf.load_ensemble(ctx, e_np)
@@ -625,53 +657,196 @@ def run_serving(args):
         torch.cuda.synchronize()
         del dB, B
         ens.append(e)
-        rng = np.random.default_rng(1000 + k)
         # request rows and phi in pinned host memory, so the server's copies are asynchronous
-        pool = torch.empty((100_000, w.n_features), dtype=torch.float32).pin_memory().numpy()
-        pool[:] = rng.standard_normal((100_000, w.n_features)).astype(np.float32)
+        pool = torch.empty((pool_rows, w.n_features), dtype=torch.float32).pin_memory().numpy()
+        pool[:] = synth.consumers(w, pool_rows)
         pools.append(pool)
-    out_rows = 2_000_000
-    out_pools = [torch.empty((out_rows, w.n_features), dtype=torch.float32).pin_memory().numpy() for w in specs]
-    out_off = [0] * len(specs)
+        out_pools.append(torch.empty((out_rows, w.n_features), dtype=torch.float32).pin_memory().numpy())
+    return specs, ctx, ens, pools, out_pools
+
+
+def _pct(v, p):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), p)) if len(v) else None
+
+
+def serving_compare(args, setup=None) -> dict:
+    """The four resident ensembles behind the continuous-batching server.
+    open_loop: Poisson arrivals (args.rate req/s for args.duration s, rows log-uniform
+    1..1e5), latency from submit to completion, small requests (at most 1,000 rows)
+    reported apart.  saturation: the first requests of the same stream (about 3M rows)
+    submitted at once, so the queue never runs dry: the server's capacity.  plain: the
+    same requests one wdf_explain call at a time from the same pinned host buffers (the
+    plain path's host-memory form).  Both serve the same device-resident ensembles, so
+    their phi are compared element by element."""
+    import torch
+
+    import paper_2511_09376_gb300 as wdf
+    from paper_2511_09376_gb300 import synth
+    dev = torch.device("cuda", 0)
+    t0 = time.time()
+    specs, ctx, ens, pools, out_pools = setup or _serving_setup(dev)
     setup_s = time.time() - t0
-    srv = wdf.server_create(ctx, ens, device_budget_bytes=16 << 30, n_slots=3, max_wave=32)
-    # warm-up: one request per ensemble
-    for k in range(len(ens)):
+    pool_rows, out_rows = pools[0].shape[0], out_pools[0].shape[0]
+    slots, max_wave, budget = 3, 32, 16 << 30
+    srv = wdf.server_create(ctx, ens, device_budget_bytes=budget, n_slots=slots, max_wave=max_wave)
+    for k in range(len(ens)):  # warm-up: one request per ensemble
         t, _ = wdf.server_submit(srv, k, pools[k][:1000])
         wdf.server_wait(srv, t, 600_000)
     wdf.server_reset_stats(srv)
+
+    def views(stream):
+        """(ensemble, rows view, phi view) of each request, cycling through the pools."""
+        offset, out_off, out = [0] * len(ens), [0] * len(ens), []
+        for _, k, n in stream:
+            o = offset[k] if offset[k] + n <= pool_rows else 0
+            offset[k] = o + n
+            p = out_off[k] if out_off[k] + n <= out_rows else 0
+            out_off[k] = p + n
+            out.append((k, pools[k][o:o + n], out_pools[k][p:p + n]))
+        return out
+
+    # open loop
     stream = synth.request_stream(synth.SEED_BASE + 5, args.rate, args.duration, len(ens))
+    reqs = views(stream)
     clocks = ClockSampler(0)
     clocks.start()
     tickets = []
     start = time.perf_counter()
-    offset = [0] * len(ens)
-    for at, k, n in stream:
+    for (at, _, _), (k, C, phi) in zip(stream, reqs):
         delay = start + at - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        o = offset[k] if offset[k] + n <= 100_000 else 0
-        offset[k] = o + n
-        p = out_off[k] if out_off[k] + n <= out_rows else 0
-        out_off[k] = p + n
-        tickets.append(wdf.server_submit(srv, k, pools[k][o:o + n], phi=out_pools[k][p:p + n])[0])
+        tickets.append(wdf.server_submit(srv, k, C, phi=phi)[0])
     for t in tickets:
         wdf.server_wait(srv, t, 600_000)
     wall = time.perf_counter() - start
-    clk = clocks.stop()
+    clk_open = clocks.stop()
     st = wdf.server_stats(srv)
-    srv.close()
+    lat = [wdf.server_request_ms(srv, t) for t in tickets]
+    small = [x for x, (_, _, n) in zip(lat, stream) if n <= 1000]
+    large = [x for x, (_, _, n) in zip(lat, stream) if n > 1000]
     offered = sum(n for _, _, n in stream) / args.duration
-    return {
-        "metric": METRIC, "value": st["rows_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(stream), "warmup": 4,
-        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": f"serving: Poisson {args.rate} req/s for {args.duration} s, rows log-uniform 1-1e5, "
-                               f"ensembles (T,D,F) = {[(w.n_trees, w.depth, w.n_features) for w in specs]}",
-                   "contraction": SPLIT_BF16, "slots": 3, "max_wave": 32, "device_budget_gb": 16},
-        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "requests": st["completed"],
-        "waves": st["waves"], "offered_rows_per_s": offered, "wall_s": wall, "setup_s": setup_s, "clocks": clk,
+    open_loop = {"rate_req_s": args.rate, "duration_s": args.duration, "requests": len(stream),
+                 "offered_rows_per_s": offered, "served_rows_per_s": st["rows_per_s"], "wall_s": wall,
+                 "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                 "small_requests": len(small), "p50_small_ms": _pct(small, 50), "p99_small_ms": _pct(small, 99),
+                 "p50_large_ms": _pct(large, 50), "p99_large_ms": _pct(large, 99), "waves": st["waves"],
+                 "clocks": clk_open}
+    # saturation: the first requests of the stream, all queued at once
+    sat_n, rows_cap = 0, 3_000_000
+    acc = 0
+    for _, _, n in stream:
+        if acc >= rows_cap:
+            break
+        acc += n
+        sat_n += 1
+    sat_reqs = views(stream[:sat_n])
+    sat_rows = sum(C.shape[0] for _, C, _ in sat_reqs)
+    wdf.server_reset_stats(srv)
+    clocks = ClockSampler(0)
+    clocks.start()
+    start = time.perf_counter()
+    tickets = [wdf.server_submit(srv, k, C, phi=phi)[0] for k, C, phi in sat_reqs]
+    for t in tickets:
+        wdf.server_wait(srv, t, 600_000)
+    sat_s = time.perf_counter() - start
+    clk_sat = clocks.stop()
+    st = wdf.server_stats(srv)
+    served_phi = [phi.copy() for _, _, phi in sat_reqs[:64]]
+    saturation = {"requests": sat_n, "rows": sat_rows, "served_rows_per_s": sat_rows / sat_s, "wall_s": sat_s,
+                  "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "waves": st["waves"], "clocks": clk_sat}
+    srv.close()
+    # the plain path on the same requests: one host-memory wdf_explain per request
+    torch.cuda.synchronize()
+    start = time.perf_counter()
+    for k, C, phi in sat_reqs:
+        wdf.explain(ens[k], C, out=phi)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - start
+    diff = max(float(np.abs(a - phi).max()) for a, (_, _, phi) in zip(served_phi, sat_reqs[:64]))
+    plain = {"rows_per_s": sat_rows / plain_s, "wall_s": plain_s,
+             "how": "one wdf_explain per request from the same pinned host buffers, in arrival order"}
+    out = {
+        "workload": f"serving: ensembles (T, D, F) = {[(w.n_trees, w.depth, w.n_features) for w in specs]}, "
+                    f"1e6-row backgrounds precomputed ({SPLIT_BF16} contraction), rows per request log-uniform 1-1e5",
+        "server": {"slots": slots, "max_wave": max_wave, "device_budget_gb": budget / 2**30, "express_slot": True},
+        "open_loop": open_loop, "saturation": saturation, "plain_same_requests": plain,
+        "served_vs_plain": plain_s / sat_s,
+        "max_abs_diff_served_vs_plain": diff,
+        "accuracy": "the same device-resident ensembles serve both arms (FP32-mode accuracy: "
+                    "tests/test_gpu_configs.py checks served rows against the FP64 oracle)",
+        "setup_s": setup_s,
     }
+    for e in ens:
+        e.close()
+    ctx.close()
+    return out
+
+
+def contraction_compare(args) -> dict:
+    """Step 3 of Algorithm 3 alone, where it is a real dense GEMM: the deep serving
+    ensembles (500 trees of depth 7, 1000 of depth 8) on their 1e6-row backgrounds.
+    wdf_set_background_counts is timed from precomputed counts in each precision (per-leaf
+    counts, scales, line maps, the contraction, the fold), and the tensor-core
+    contraction kernel alone with the launch list's events."""
+    import torch
+
+    import paper_2511_09376_gb300 as wdf
+    from paper_2511_09376_gb300 import synth
+    peaks, kind = _peaks()
+    ctx = wdf.ctx_create(0)
+    dev = torch.device("cuda", 0)
+    out = {}
+    for w in synth.serving_specs()[2:]:
+        e_np, _, B = synth.make(w)
+        e = wdf.load_ensemble(ctx, e_np)
+        counts = wdf.background_counts(e, torch.from_numpy(B).to(dev))
+        m = B.shape[0]
+        del B
+        info = wdf.ensemble_info(e)
+        D, live = info["depth"], info["n_live_leaves"]
+        K, N = 1 << D, D << D
+        r = {"trees": w.n_trees, "depth": D, "live_leaves": live, "gemm": f"{live} x {K} x {N} (M x K x N)"}
+        for prec, products in (("fp32", 1), ("tf32x3", 3), ("bf16x6", 6)):
+            wdf.set_background_counts(e, counts, m, prec)  # warm-up (splits the tables once)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            reps = 5
+            ev[0].record()
+            for _ in range(reps):
+                wdf.set_background_counts(e, counts, m, prec)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / reps
+            flops = 2.0 * live * K * N
+            r[prec] = {"set_background_counts_ms": ms, "dense_gemm_tflops": flops / (ms * 1e-3) / 1e12,
+                       "tensor_products": products if prec != "fp32" else 0}
+        r["bf16x6_vs_fp32"] = r["fp32"]["set_background_counts_ms"] / r["bf16x6"]["set_background_counts_ms"]
+        out[f"T{w.n_trees}_D{D}"] = r
+        e.close()
+    ctx.close()
+    out["peak_bf16_tflops"] = peaks.get("bf16_tflops")
+    out["peak_kind"] = kind
+    return out
+
+
+def run_ragged(args):
+    """--workload ragged: the ragged comparison as the JSON line (value = batched rows/s)."""
+    r = ragged_compare(args)
+    return {"metric": METRIC, "value": r["batched"]["rows_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": r["steps"], "warmup": args.warmup, "ms_per_step": r["batched"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": r["workload"]}, "ragged": r}
+
+
+def run_serving(args):
+    """--workload serving: the serving comparison as the JSON line (value = open-loop
+    served rows/s)."""
+    r = serving_compare(args)
+    return {"metric": METRIC, "value": r["open_loop"]["served_rows_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": r["open_loop"]["requests"], "warmup": 4, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": r["workload"]}, "serving": r}
 
 
 def main():
@@ -690,7 +865,10 @@ def main():
     ap.add_argument("--shard-background", action="store_true",
                     help="N > 1: each rank counts 1/N of the background rows, the counts are summed over ranks")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
-    ap.add_argument("--duration", type=float, default=30.0, help="serving: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
+    ap.add_argument("--ragged-steps", type=int, default=5, help="ragged: timed steps of each arm")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the ragged-batch and serving comparisons of the default run")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -706,6 +884,9 @@ def main():
     if args.workload == "serving":
         print(json.dumps(run_serving(args)), flush=True)
         return
+    if args.workload == "contraction":
+        print(json.dumps({"contraction": contraction_compare(args)}), flush=True)
+        return
     if args.workload == "interactions":
         print(json.dumps(run_interactions(args)), flush=True)
         return
@@ -718,6 +899,17 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(ens, C, B)
+        del ens, C, B
+        if world == 1 and args.workload == "large" and not args.no_forms:
+            # the metric's comparison on the same box and run: the batched and served
+            # forms against the plain path
+            import torch
+            torch.cuda.empty_cache()
+            result["ragged"] = ragged_compare(args)
+            torch.cuda.empty_cache()
+            result["serving"] = serving_compare(args)
+            torch.cuda.empty_cache()
+            result["contraction"] = contraction_compare(args)
         print(json.dumps(result), flush=True)
     if world > 1:
         import torch.distributed as dist
