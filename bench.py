@@ -113,7 +113,7 @@ class ClockSampler:
 
 
 # sources whose hash a committed ncu summary must match for its counters to stand
-EXPLAIN_SOURCES = ["k_explain.cuh", "k_explain.cu", "k_codes.cu", "wdf_device.cuh", "tree_layout.h"]
+EXPLAIN_SOURCES = ["k_explain.cuh", "k_explain.cu", "k_codes.cu", "wdf_device.cuh", "tree_layout.h", "launch.h"]
 BACKGROUND_SOURCES = ["k_background.cu", "k_codes.cu", "wdf_device.cuh", "tree_layout.h"]
 
 
@@ -180,6 +180,35 @@ def algorithmic_ops(ens) -> dict:
                 stack.append((int(ens.left[o + v]), feats + (f,)))
                 stack.append((int(ens.right[o + v]), feats + (f,)))
     return {"compares": compares, "lookup_adds": adds, "ops": compares + adds}
+
+
+def l1_floor(ens, D: int) -> dict:
+    """The fewest L1 data-pipe wavefronts a consumer row needs in the consumer kernel's
+    design (one wavefront moves 128 bytes for a warp of 32 rows): one gather of the
+    folded slot vector (4 * SP bytes, SP = D + 1 slots padded to 4, 8 or 12) per live
+    bottom subtree, i.e. the subtrees of height 2 holding a non-zero leaf, and one read
+    plus one write of the row's 4-byte phi accumulator per real inner node."""
+    sp = 4 if D + 1 <= 4 else (8 if D + 1 <= 8 else 12)
+    live = real = 0
+    for t in range(ens.n_trees):
+        o = int(ens.tree_offset[t])
+        stack, subs = [(0, 0, 0)], set()
+        while stack:
+            v, h, d = stack.pop()
+            if int(ens.feature[o + v]) < 0:
+                if float(ens.value[o + v]) != 0.0:
+                    # a leaf at depth d is pushed left down to depth D: leaf q of the complete layout
+                    q = (h + 1) * (1 << (D - d)) - 1 - ((1 << D) - 1)
+                    subs.add(q // 4)
+            else:
+                real += 1
+                stack.append((int(ens.left[o + v]), 2 * h + 1, d + 1))
+                stack.append((int(ens.right[o + v]), 2 * h + 2, d + 1))
+        live += len(subs)
+    gather = live * 4 * sp / 128.0
+    phi = 2.0 * real / 32.0
+    return {"live_subtree_gathers": live, "real_inner_nodes": real, "wavefronts_per_row": gather + phi,
+            "gather_wavefronts_per_row": gather, "phi_wavefronts_per_row": phi}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -286,6 +315,8 @@ def run_ours(args, rank, world, local_rank):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak_max = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = ops["ops"] * n / (explain_ms * 1e-3) / 1e12
+    l1 = l1_floor(ens, info["depth"])
+    l1_peak = sms * peaks.get("sm_max_mhz", 2070.0) * 1e6
     # background: one compare per inner node and one count per (row, live leaf)
     bg_ops = ops["compares"] + info["n_live_leaves"]
     hbm_bytes = 2 * n * F * 4
@@ -310,7 +341,7 @@ def run_ours(args, rank, world, local_rank):
         "reduce_ms": ms - explain_ms - background_ms,
         "explain_only_rows_per_s": world * n / (explain_ms * 1e-3),
         "roofline": {
-            "kernel": "the explain call: k_encode_codes + k_explain (codes, patterns, gathers, phi accumulation)",
+            "kernel": "the explain call: one k_explain launch (codes, patterns, gathers, phi accumulation)",
             "bound": "alu",
             "achieved": achieved,
             "peak": alu_peak_max,
@@ -323,10 +354,15 @@ def run_ours(args, rank, world, local_rank):
             "peak_basis": f"{sms} SMs x 128 lanes/clk x {peaks.get('sm_max_mhz', 2070.0)} MHz (max SM clock, {peak_kind})",
             "hbm_gbs": hbm_bytes / (explain_ms * 1e-3) / 1e9,
             "hbm_frac_of_measured": hbm_bytes / (explain_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            # against the L1 data pipe (the resource ncu shows bounding the kernel): the
+            # fewest wavefronts the design needs per row, at one wavefront per SM per clock
+            "l1_floor": {**l1, "peak_wavefronts_per_s": l1_peak,
+                         "achieved_floor_wavefronts_per_s": l1["wavefronts_per_row"] * n / (explain_ms * 1e-3),
+                         "frac": l1["wavefronts_per_row"] * n / (explain_ms * 1e-3) / l1_peak},
         },
         "roofline_background": {
-            "kernel": "set_background: k_encode_codes + k_bg_hist (codes, patterns, joint counts) + the small "
-                      "per-leaf, contraction and fold kernels",
+            "kernel": "set_background: k_encode_codes (on a side stream, overlapping) + k_bg_hist (patterns, "
+                      "joint counts) + the small per-leaf, line-map, contraction and fold kernels",
             "bound": "alu",
             "achieved": bg_ops * m / (background_ms * 1e-3) / 1e12,
             "peak": alu_peak_max,
@@ -687,7 +723,7 @@ def serving_compare(args, setup=None) -> dict:
     specs, ctx, ens, pools, out_pools = setup or _serving_setup(dev)
     setup_s = time.time() - t0
     pool_rows, out_rows = pools[0].shape[0], out_pools[0].shape[0]
-    slots, max_wave, budget = 3, 32, 16 << 30
+    slots, max_wave, budget = 4, 32, 16 << 30
     srv = wdf.server_create(ctx, ens, device_budget_bytes=budget, n_slots=slots, max_wave=max_wave)
     for k in range(len(ens)):  # warm-up: one request per ensemble
         t, _ = wdf.server_submit(srv, k, pools[k][:1000])
@@ -797,8 +833,9 @@ def contraction_compare(args) -> dict:
     ctx = wdf.ctx_create(0)
     dev = torch.device("cuda", 0)
     out = {}
-    for w in synth.serving_specs()[2:]:
-        e_np, _, B = synth.make(w)
+    specs = synth.serving_specs()[3:] if args.deep_only else synth.serving_specs()[2:]
+    for w in specs:
+        e_np, _, B = synth.make(w, n_background=args.background)
         e = wdf.load_ensemble(ctx, e_np)
         counts = wdf.background_counts(e, torch.from_numpy(B).to(dev))
         m = B.shape[0]
@@ -867,6 +904,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--ragged-steps", type=int, default=5, help="ragged: timed steps of each arm")
+    ap.add_argument("--deep-only", action="store_true",
+                    help="contraction: only the depth-8 ensemble (for profiler captures)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the ragged-batch and serving comparisons of the default run")
     args = ap.parse_args()

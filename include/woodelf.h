@@ -160,9 +160,9 @@ wdf_status wdf_set_metric(wdf_ensemble *ens, wdf_metric metric);
  * phi[c, i] for the n consumer rows C (leading dimension ldc) into phi (leading
  * dimension ldphi >= F): Algorithm 3 step 4 / Eq. "bg_shap_derivation" step (g).
  * C and phi live in the same memory kind.  WDF_EINVAL if no background was set.
- * Device kind: asynchronous and allocation-free: every block computes its rows'
- * decision codes in shared memory, so calls on different streams share no scratch
- * memory.  Host kind: copies
+ * Device kind: asynchronous; the rows' decision codes (one or two bytes per code column
+ * and row, at most 2^20 rows at a time) live in a temporary stream-ordered allocation,
+ * so calls on different streams never share scratch memory.  Host kind: copies
  * through the ensemble's device staging buffers and returns once phi is written on the
  * host.  phi of a row does not depend on the other rows of the call (the same
  * floating-point additions in the same order).
@@ -244,7 +244,7 @@ wdf_status wdf_batch_tile_rows(const wdf_batch *batch, int32_t depth, int32_t *t
  * work, or the next part's device buffers (2 * rows * F * 4 bytes) would exceed
  * device_budget_bytes; it runs the wave as copies in, ONE batch launch
  * (wdf_batch_explain) and copies out on the slot's stream.  Waves of different slots
- * overlap on the GPU.  With two or more slots, slot 0 is an express slot: it takes only
+ * overlap on the GPU.  With four or more slots, slot 0 is an express slot: it takes only
  * requests of at most 2^20 rows x trees of remaining work, in waves of at most 2^22
  * rows x trees, so small requests do not queue behind large parts.  A request whose next part does not fit the remaining
  * budget is passed over for smaller ones at most 8 fills in a row; then the fill stops

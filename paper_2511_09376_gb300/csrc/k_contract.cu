@@ -169,8 +169,8 @@ __global__ void k_fold(int D, const float *__restrict__ S, const int32_t *__rest
         for (int k = 0; k <= D - 2; ++k) out[k] += __ldg(Sr + ((size_t)k << D) + p);
         out[(j < 2) ? D - 1 : D] += __ldg(Sr + ((size_t)(D - 1) << D) + p);
     }
-    const uint32_t map = (__ldg(lines + (size_t)t * lines_words(D) + (s >> 2)) >> (8 * (s & 3))) & 0xFFu;
-    const int64_t at = ((int64_t)t * NS + s) * E + line_pos((uint32_t)e, map);
+    const uint32_t rot = (__ldg(lines + (size_t)t * lines_words(D) + (s >> 2)) >> (8 * (s & 3))) & 0xFFu;
+    const int64_t at = ((int64_t)t * NS + s) * E + line_pos((uint32_t)e, rot, D);
     float4 *dst = reinterpret_cast<float4 *>(sfold + at * SP);
     for (int k = 0; k < SP; k += 4) dst[k / 4] = make_float4(out[k], out[k + 1], out[k + 2], out[k + 3]);
 }
@@ -183,53 +183,47 @@ cudaError_t launch_fold(int D, const float *S, const int32_t *leaf_row, int T, c
     return cudaGetLastError();
 }
 
-// One thread per (tree, word of line maps): for each of its (up to) four subtrees, the
-// background frequency of every entry bit b (the share of rows with bit b set); the two
-// bits nearest one half become b0 < b1.  Ties keep the lower bit; a subtree no row
-// reaches keeps the identity.
-__global__ void k_line_maps(int D, const uint32_t *__restrict__ hist, int T, uint32_t *__restrict__ lines) {
-    const int NS = 1 << (D - 2), E = 1 << (D + 1), W = lines_words(D);
+// One thread per (tree, map byte): for its bottom subtree s, the background frequency of
+// every entry bit b (the share of rows with bit b set), and the rotation r whose low
+// pair (bits r and r + 1 mod D + 1) is the least certain: the largest sum of
+// min(p, 1 - p).  Ties keep the smaller r; a subtree no row reaches, and the padding
+// bytes past the last subtree, keep the identity 0.
+__global__ void k_line_maps(int D, const uint32_t *__restrict__ hist, int T, uint8_t *__restrict__ lines) {
+    const int NS = 1 << (D - 2), E = 1 << (D + 1), B = 4 * lines_words(D), NB = D + 1;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)T * W) return;
-    const int t = (int)(idx / W), w = (int)(idx % W);
-    uint32_t word = 0;
-    for (int q = 0; q < 4; ++q) {
-        const int s = 4 * w + q;
-        uint32_t map = 0x10u;
-        if (s < NS && hist) {
-            const uint32_t *h = hist + ((size_t)t * NS + s) * E;
-            double total = 0.0, ones[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            for (int e = 0; e < E; ++e) {
-                const double c = (double)__ldg(h + e);
-                total += c;
-                for (int b = 0; b <= D; ++b)
-                    if ((e >> b) & 1) ones[b] += c;
-            }
-            if (total > 0.0) {
-                int best0 = 0, best1 = 1;
-                double u0 = -1.0, u1 = -1.0;  // u0 >= u1: the two largest uncertainties
-                for (int b = 0; b <= D; ++b) {
-                    const double pb = ones[b] / total, u = pb < 1.0 - pb ? pb : 1.0 - pb;
-                    if (u > u0) {
-                        u1 = u0; best1 = best0;
-                        u0 = u; best0 = b;
-                    } else if (u > u1) {
-                        u1 = u; best1 = b;
-                    }
+    if (idx >= (int64_t)T * B) return;
+    const int t = (int)(idx / B), s = (int)(idx % B);
+    uint32_t rot = 0;
+    if (s < NS && hist) {
+        const uint32_t *h = hist + ((size_t)t * NS + s) * E;
+        uint64_t total = 0, ones[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int e = 0; e < E; ++e) {
+            const uint64_t c = __ldg(h + e);
+            total += c;
+            for (int b = 0; b < NB; ++b) ones[b] += ((e >> b) & 1) ? c : 0;
+        }
+        if (total > 0) {
+            double best = -1.0;
+            for (int r = 0; r < NB; ++r) {
+                double u = 0.0;
+                for (int k = 0; k < 2; ++k) {
+                    const double p = (double)ones[(r + k) % NB] / (double)total;
+                    u += p < 1.0 - p ? p : 1.0 - p;
                 }
-                const int b0 = best0 < best1 ? best0 : best1, b1 = best0 < best1 ? best1 : best0;
-                map = ((uint32_t)b1 << 4) | (uint32_t)b0;
+                if (u > best) {
+                    best = u;
+                    rot = (uint32_t)r;
+                }
             }
         }
-        word |= map << (8 * q);
     }
-    lines[idx] = word;
+    lines[idx] = (uint8_t)rot;
 }
 
 cudaError_t launch_line_maps(int D, const uint32_t *hist, int T, uint32_t *lines, cudaStream_t st) {
-    const int64_t total = (int64_t)T * lines_words(D);
+    const int64_t total = (int64_t)T * 4 * lines_words(D);
     if (total == 0) return cudaSuccess;
-    k_line_maps<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(D, hist, T, lines);
+    k_line_maps<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(D, hist, T, reinterpret_cast<uint8_t *>(lines));
     count_launches(1);
     return cudaGetLastError();
 }

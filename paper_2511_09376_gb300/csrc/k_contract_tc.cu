@@ -200,8 +200,10 @@ __global__ void k_pack_b(int D, const float *__restrict__ t32, int G, int NT, in
     }
 }
 
-// One CTA: the 128-row tile blockIdx.x (of signature group tiles[.].x) times the column
-// block blockIdx.y (NT columns), over nk K steps through a ring of `ring` stages.
+// One CTA: a 128-row tile (of signature group tiles[.].x) times a column block of NT
+// columns, over nk K steps through a ring of `ring` stages.  The column blocks of one
+// tile are consecutive CTAs (blockIdx.x = tile * NB + block), so they run together and
+// read the tile's A stages from L2 rather than each from HBM.
 template <bool BF16, int NP>
 __global__ void __launch_bounds__(128) k_contract_tc(int D, const unsigned char *__restrict__ apk,
                                                      const unsigned char *__restrict__ bpk,
@@ -210,9 +212,10 @@ __global__ void __launch_bounds__(128) k_contract_tc(int D, const unsigned char 
                                                      int *__restrict__ err, uint32_t first_limit) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int N = D << D;
-    const int4 tile = tiles[blockIdx.x];
+    const int ti = (int)(blockIdx.x / (unsigned)NB), nb = (int)(blockIdx.x % (unsigned)NB);
+    const int4 tile = tiles[ti];
     const int g = tile.x, r0 = tile.y, r1 = tile.z;
-    const int nb = blockIdx.y, n0 = nb * NT;
+    const int n0 = nb * NT;
     const uint32_t a_bytes = (uint32_t)NP * kRows * kStepBytes, b_bytes = (uint32_t)NP * NT * kStepBytes;
     const uint32_t stage_bytes = a_bytes + b_bytes;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)ring * stage_bytes);
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(128) k_contract_tc(int D, const unsigned char 
     bool failed = false;
     if (tid == 0) {
         // copies run ring - 1 stages ahead of the MMAs
-        const unsigned char *asrc = apk + (size_t)blockIdx.x * nk * a_bytes;
+        const unsigned char *asrc = apk + (size_t)ti * nk * a_bytes;
         const unsigned char *bsrc = bpk + ((size_t)g * NB + nb) * nk * b_bytes;
         const uint32_t idesc = instr_desc(BF16, NT, kRows);
         const uint32_t smem0 = smem_u32(smem);
@@ -395,8 +398,7 @@ cudaError_t launch_contract_tc(int D, int mode, const float *A, const float *sca
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e != cudaSuccess) return e;
     const uint32_t first = g_first_wait_limit.load();
-    dim3 grid(n_tiles, g.NB);
-    kern<<<grid, 128, g.smem, st>>>(D, apk, bpk, scale, tiles, S, g.NT, g.NB, g.nk, g.ring, err,
+    kern<<<(unsigned)((int64_t)n_tiles * g.NB), 128, g.smem, st>>>(D, apk, bpk, scale, tiles, S, g.NT, g.NB, g.nk, g.ring, err,
                                     first ? first : kWaitLimit);
     count_launches(1);
     return cudaGetLastError();

@@ -15,12 +15,12 @@ WDF_EXPLAIN_DEPTH(7, extern)
 WDF_EXPLAIN_DEPTH(8, extern)
 
 template <int D>
-static cudaError_t explain_depth(const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi,
+static cudaError_t explain_depth(const unsigned char *codes, int64_t n, const ExplainJob &job, float *phi,
                                  int64_t ldp, int tile_rows, const DevInfo &dev, cudaStream_t st) {
     switch (tile_rows) {
-        case 32: return explain_t<D, 32>(C, n, ldc, job, phi, ldp, dev, st);
-        case 128: return explain_t<D, 128>(C, n, ldc, job, phi, ldp, dev, st);
-        default: return explain_t<D, 64>(C, n, ldc, job, phi, ldp, dev, st);
+        case 32: return explain_t<D, 32>(codes, n, job, phi, ldp, dev, st);
+        case 128: return explain_t<D, 128>(codes, n, job, phi, ldp, dev, st);
+        default: return explain_t<D, 64>(codes, n, job, phi, ldp, dev, st);
     }
 }
 
@@ -39,9 +39,9 @@ int default_tile_rows(int D, int F, int xb, const DevInfo &dev) {
     return s64 <= dev.smem_optin / 2 ? 64 : 32;
 }
 
-// Launches are cut at 2^24 rows so that the block index stays well inside the grid limit
-// and a single launch's duration stays bounded.
-constexpr int64_t kExplainLaunchRows = 1 << 24;
+// Rows per encoded chunk: the decision codes of a chunk live in a stream-ordered
+// scratch allocation (so concurrent calls on other streams never share it).
+constexpr int64_t kExplainChunkRows = 1 << 20;
 
 cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi,
                            int64_t ldp, int tile_rows, const DevInfo &dev, cudaStream_t st) {
@@ -49,22 +49,29 @@ cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const 
     if (D < 2 || D > 8) return cudaErrorInvalidValue;
     const int xb = job.ta.n_cols * job.ta.code_bytes;
     if (tile_rows <= 0) tile_rows = default_tile_rows(D, job.F, xb, dev);
-    cudaError_t err = cudaSuccess;
-    for (int64_t r0 = 0; r0 < n && err == cudaSuccess; r0 += kExplainLaunchRows) {
-        const int64_t rows = std::min(kExplainLaunchRows, n - r0);
-        const float *in = C + r0 * ldc;
+    const int64_t chunk = std::min(n, kExplainChunkRows);
+    const int64_t pad = 128;  // every tile size divides it
+    unsigned char *codes = nullptr;
+    cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&codes), (size_t)((chunk + pad - 1) / pad * pad) * xb,
+                                      st);
+    if (err != cudaSuccess) return err;
+    for (int64_t r0 = 0; r0 < n && err == cudaSuccess; r0 += chunk) {
+        const int64_t rows = std::min(chunk, n - r0);
+        err = launch_encode_codes(C + r0 * ldc, rows, ldc, job.ta, (rows + pad - 1) / pad * pad, codes, st);
+        if (err != cudaSuccess) break;
         float *out = phi + r0 * ldp;
         switch (D) {
-            case 2: err = explain_depth<2>(in, rows, ldc, job, out, ldp, tile_rows, dev, st); break;
-            case 3: err = explain_depth<3>(in, rows, ldc, job, out, ldp, tile_rows, dev, st); break;
-            case 4: err = explain_depth<4>(in, rows, ldc, job, out, ldp, tile_rows, dev, st); break;
-            case 5: err = explain_depth<5>(in, rows, ldc, job, out, ldp, tile_rows, dev, st); break;
-            case 6: err = explain_depth<6>(in, rows, ldc, job, out, ldp, tile_rows, dev, st); break;
-            case 7: err = explain_depth<7>(in, rows, ldc, job, out, ldp, tile_rows, dev, st); break;
-            default: err = explain_depth<8>(in, rows, ldc, job, out, ldp, tile_rows, dev, st); break;
+            case 2: err = explain_depth<2>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            case 3: err = explain_depth<3>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            case 4: err = explain_depth<4>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            case 5: err = explain_depth<5>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            case 6: err = explain_depth<6>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            case 7: err = explain_depth<7>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+            default: err = explain_depth<8>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
         }
     }
-    return err;
+    const cudaError_t ferr = cudaFreeAsync(codes, st);
+    return err != cudaSuccess ? err : ferr;
 }
 
 cudaError_t launch_explain_batch(int D, const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items,

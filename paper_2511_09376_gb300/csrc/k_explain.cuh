@@ -121,10 +121,22 @@ __device__ __forceinline__ void encode_tile(const float *__restrict__ C, int64_t
     constexpr int IL = 16;  // searches in flight per thread: their threshold loads are mostly L2 round trips
     const int FS = F | 1;
     const int rows = (int)min((int64_t)TC, n - c0);
-    for (int r = tid / 32; r < TC; r += TC / 32) {  // one warp per row at a time: coalesced
+    // every element of the tile in flight at once (asynchronous 4-byte copies; the rows
+    // come from HBM, so element-by-element loads would serialise their latency)
+    for (int r = tid / 32; r < TC; r += TC / 32) {
         const float *src = C + (c0 + r) * ldc;
-        for (int f = tid & 31; f < F; f += 32) stage[r * FS + f] = r < rows ? __ldg(src + f) : 0.0f;
+        for (int f = tid & 31; f < F; f += 32) {
+            float *dst = stage + r * FS + f;
+            if (r < rows)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                                 static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                             "l"(src + f)
+                             : "memory");
+            else
+                *dst = 0.0f;
+        }
     }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     const int lane = tid & 31, warp = tid >> 5, row = warp * 32 + lane;
     const bool valid = row < rows;
@@ -168,11 +180,17 @@ __device__ __forceinline__ void encode_tile(const float *__restrict__ C, int64_t
     __syncthreads();
 }
 
-// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble: the
-// rows' decision codes are computed here from C (encode_tile), then every tree.
-template <int D, int TC>
+// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble.  ENC:
+// the rows' decision codes are computed here from C (encode_tile); otherwise they are
+// copied from codes, the code blocks of all n rows written by k_encode_codes (padded
+// to a multiple of TC rows).  The plain path encodes in a kernel of its own: in-tile
+// encoding measured 1.9 ms per 1M rows slower at the large workload (ten warps per SM
+// cannot hide the dependent threshold loads of the searches), so only the ragged batch,
+// whose rows arrive in one graph launch, encodes in the tile.
+template <int D, int TC, bool ENC>
 __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float *__restrict__ C, int64_t n,
-                                             int64_t ldc, float *__restrict__ phi, int64_t ldp, int64_t c0,
+                                             int64_t ldc, const unsigned char *__restrict__ codes,
+                                             float *__restrict__ phi, int64_t ldp, int64_t c0,
                                              unsigned char *smem_raw) {
     using S = Shape<D>;
     using X = ExplainCfg<D>;
@@ -192,7 +210,12 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
     int4 *srec = reinterpret_cast<int4 *>(smem_raw + L.x + L.p + L.meta);
     int *sfl = reinterpret_cast<int *>(smem_raw + L.x + L.p + L.meta + L.rec);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    encode_tile<TC>(C, n, ldc, c0, ta, F, sp, sx, tid);
+    if constexpr (ENC) {
+        encode_tile<TC>(C, n, ldc, c0, ta, F, sp, sx, tid);
+    } else {
+        const uint4 *src = reinterpret_cast<const uint4 *>(codes + c0 * xb);
+        for (int i = tid; i < TC * xb / 16; i += TC) reinterpret_cast<uint4 *>(sx)[i] = __ldg(src + i);
+    }
     for (int i = tid; i < (F + 1) * XS; i += TC) sp[i] = 0.0f;
     float *myphi = sp + tid;
     const CodeReader xr(sx + (size_t)warp * 32 * xb, lane, cb);
@@ -213,7 +236,9 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
             const int *fl = sfl + g * FL;
             uint32_t dw[S::NW];
             // one generic decision loop for both code widths (a second, one-byte copy in
-            // this loop measured slower here, unlike in the counting kernel)
+            // this loop measured slower here, unlike in the counting kernel; node words
+            // packed four to a 16-byte load measured slower too: the decoding cost more
+            // issue slots than the shared-memory wavefronts it saved)
             tree_decisions<D, false>(srec + g * S::NI, mt, xr, dw);
             uint32_t ent[S::NS];
             subtree_entries<D>(dw, ent);
@@ -239,8 +264,8 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
 #pragma unroll
                 for (int j = 0; j < GS; ++j) {
                     const uint32_t lj = (uint32_t)(lv >> (s0 + j)) & 1u;
-                    const uint32_t map = (lmap[(s0 + j) >> 2] >> (8 * ((s0 + j) & 3))) & 0xFFu;
-                    const float4 *src = tf + ((size_t)(s0 + j) * S::E + line_pos(ent[s0 + j], map)) * Q;
+                    const uint32_t rot = (lmap[(s0 + j) >> 2] >> (8 * ((s0 + j) & 3))) & 0xFFu;
+                    const float4 *src = tf + ((size_t)(s0 + j) * S::E + line_pos(ent[s0 + j], rot, D)) * Q;
 #pragma unroll
                     for (int k = 0; k < Q; ++k) v[j][k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     if (Q == 2) {
@@ -314,10 +339,10 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
 // 1 block per SM is enough (shared memory limits residency anyway): the register
 // budget then covers a whole gather group in flight.
 template <int D, int TC>
-__global__ void __launch_bounds__(TC, 1) k_explain(const float *__restrict__ C, int64_t n, int64_t ldc,
+__global__ void __launch_bounds__(TC, 1) k_explain(const unsigned char *__restrict__ codes, int64_t n,
                                                    ExplainJob job, float *__restrict__ phi, int64_t ldp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    explain_tile<D, TC>(job, C, n, ldc, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
+    explain_tile<D, TC, false>(job, nullptr, n, 0, codes, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
 }
 
 // Persistent form over a ragged batch: work item i is (job, request, first row).  Blocks
@@ -342,13 +367,13 @@ __global__ void __launch_bounds__(TC, 1) k_explain_batch(const ExplainJob *__res
         const ExplainJob job = jobs[it.x];
         const BatchRequest rq = reqs[it.y];
         const int64_t c0 = ((int64_t)it.z << 31) | (uint32_t)it.w;
-        explain_tile<D, TC>(job, rq.C, rq.n, rq.ldc, rq.phi, rq.ldp, c0, smem_raw);
+        explain_tile<D, TC, true>(job, rq.C, rq.n, rq.ldc, nullptr, rq.phi, rq.ldp, c0, smem_raw);
         __syncthreads();
     }
 }
 
 template <int D, int TC>
-cudaError_t explain_t(const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi, int64_t ldp,
+cudaError_t explain_t(const unsigned char *codes, int64_t n, const ExplainJob &job, float *phi, int64_t ldp,
                       const DevInfo &dev, cudaStream_t st) {
     const size_t smem = ExLayout<D>(job.F, job.ta.n_cols * job.ta.code_bytes, TC).total;
     if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
@@ -356,7 +381,7 @@ cudaError_t explain_t(const float *C, int64_t n, int64_t ldc, const ExplainJob &
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     const int64_t blocks = (n + TC - 1) / TC;
-    kern<<<(unsigned)blocks, TC, smem, st>>>(C, n, ldc, job, phi, ldp);
+    kern<<<(unsigned)blocks, TC, smem, st>>>(codes, n, job, phi, ldp);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -383,7 +408,7 @@ cudaError_t batch_t(const ExplainJob *jobs, const BatchRequest *reqs, const int4
 // Explicit instantiation of the kernels of one (depth, tile rows) pair; each pair is
 // compiled in one of the k_explain_d*.cu translation units.
 #define WDF_EXPLAIN_TILE(d, tc, spec)                                                                            \
-    spec template cudaError_t explain_t<d, tc>(const float *, int64_t, int64_t, const ExplainJob &, float *,     \
+    spec template cudaError_t explain_t<d, tc>(const unsigned char *, int64_t, const ExplainJob &, float *,       \
                                                int64_t, const DevInfo &, cudaStream_t);                          \
     spec template cudaError_t batch_t<d, tc>(const ExplainJob *, const BatchRequest *, const int4 *, int *, int,  \
                                              int, int, const DevInfo &, cudaStream_t);

@@ -33,17 +33,15 @@ struct ExplainJob {
 // Where the consumer gathers land.  A warp's 32-byte gathers of one bottom subtree are
 // served a quarter warp at a time, one L1 wavefront per distinct 128-byte line, and a
 // line holds four consecutive entries.  Entries are formed from D + 1 decision bits;
-// the two bits whose background frequency is closest to one half are moved to the two
-// lowest positions (within a line), so the rows of a quarter warp, which mostly agree on
-// the more certain decisions, land in fewer lines.  The map of subtree s is one byte,
-// (b1 << 4) | b0 with b0 < b1: swap bit 0 with bit b0, then bit 1 with bit b1 (a
-// permutation of the entries; 0x10 is the identity).
-__host__ __device__ __forceinline__ uint32_t line_pos(uint32_t e, uint32_t map) {
-    const uint32_t b0 = map & 15u, b1 = map >> 4;
-    uint32_t x = (e ^ (e >> b0)) & 1u;
-    e ^= x | (x << b0);
-    x = ((e >> 1) ^ (e >> b1)) & 1u;
-    return e ^ ((x << 1) | (x << b1));
+// the entry of subtree s is stored rotated right by r_s bits, r_s chosen so that the two
+// bits that land in the two lowest positions (within a line) are the adjacent pair
+// (cyclically) whose background frequencies are closest to one half: the rows of a
+// quarter warp mostly agree on the more certain decisions, so they land in fewer lines.
+// The map of subtree s is the byte r_s (0 is the identity).  A rotation keeps nearly all
+// of the gain of moving the best two bits anywhere, for a third of the instructions.
+__host__ __device__ __forceinline__ uint32_t line_pos(uint32_t e, uint32_t r, int D) {
+    const uint32_t nb = (uint32_t)D + 1u;
+    return ((e >> r) | (e << (nb - r))) & ((1u << nb) - 1u);
 }
 // 32-bit words of line maps per tree: one byte per bottom subtree, at least four words
 // so that a tree's maps are whole 16-byte loads.

@@ -40,6 +40,7 @@ constexpr int64_t kPartRows = 8192;         // rows per part of a request
 constexpr int64_t kWaveWork = 16ll << 20;    // row-trees per wave (rows x trees of the ensemble)
 constexpr int64_t kSmallWork = 1ll << 20;    // largest request (row-trees) of the express slot
 constexpr int64_t kExpressWaveWork = 4ll << 20;  // row-trees per express wave: short waves
+constexpr int kExpressMinSlots = 4;              // slot 0 is the express slot from this many slots on
 constexpr int kMaxSkips = 8;                 // fills that may pass over a request that does not fit
 
 struct Request {
@@ -190,7 +191,7 @@ int64_t remaining_work(const wdf_server *s, const Request &r) {
 }
 
 // Fill a wave for a free slot from the queue, one part per request per pass.  The
-// express slot (slot 0 when there are two or more) takes only requests whose remaining
+// express slot (slot 0 when there are four or more) takes only requests whose remaining
 // work is at most kSmallWork, in waves of at most kExpressWaveWork, so a small request
 // never waits behind the large parts that occupy the other slots.  A part that does not fit the remaining device budget is
 // skipped (a smaller one further back may fit), but once a request has been passed over
@@ -199,7 +200,7 @@ int64_t remaining_work(const wdf_server *s, const Request &r) {
 Wave fill_wave(wdf_server *s, int slot) {
     Wave w;
     w.slot = slot;
-    const bool express = s->n_slots >= 2 && slot == 0;
+    const bool express = s->n_slots >= kExpressMinSlots && slot == 0;
     const int64_t wave_work = express ? kExpressWaveWork : kWaveWork;
     int64_t work = 0;
     bool added = true, blocked = false;
@@ -276,7 +277,7 @@ void run(wdf_server *s) {
             if (!s->wave[(size_t)k].parts.empty()) continue;
             Wave w = fill_wave(s, k);
             if (w.parts.empty()) {
-                if (s->n_slots >= 2 && k == 0) continue;  // no small request queued: try the other slots
+                if (s->n_slots >= kExpressMinSlots && k == 0) continue;  // no small request: try the others
                 break;                                    // no part fits until memory frees up
             }
             s->in_use += w.bytes;

@@ -124,13 +124,12 @@ def test_multi_part_requests_strided_across_waves_and_slots(setup):
 
 
 def test_small_requests_use_the_express_slot(setup):
-    """With two or more slots, small requests are served while large parts hold the
-    other slots: a single-row request submitted behind many large parts completes
-    before them."""
+    """With four or more slots, slot 0 serves only small requests: a single-row request
+    submitted behind many large parts completes before them."""
     wdf, ctx, ens = setup
     F = wdf.ensemble_info(ens[1])["n_features"]
-    srv = wdf.server_create(ctx, ens, device_budget_bytes=4 << 30, n_slots=2, max_wave=1)
-    big = [wdf.server_submit(srv, 1, _rows(1, 60000, F, 900 + i)) for i in range(4)]
+    srv = wdf.server_create(ctx, ens, device_budget_bytes=4 << 30, n_slots=4, max_wave=1)
+    big = [wdf.server_submit(srv, 1, _rows(1, 60000, F, 900 + i)) for i in range(8)]
     t_small, phi_small = wdf.server_submit(srv, 1, _rows(1, 1, F, 999))
     wdf.server_wait(srv, t_small)
     done_big = sum(wdf.server_poll(srv, t) for t, _ in big)
