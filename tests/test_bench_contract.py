@@ -29,3 +29,16 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_does_not_load_the_cuda_library():
+    """The reference arm imports the input generator and the oracle only: the package
+    loads libwoodelf.so on first use of a binding name, never on import."""
+    code = ("import sys; sys.path.insert(0, '.'); "
+            "from paper_2511_09376_gb300 import synth; import oracle; oracle.build(); "
+            "e, C, B = synth.make('tiny'); oracle.values_hist(e, oracle.bg_hist(e, B), B.shape[0], C[:2]); "
+            "maps = open('/proc/self/maps').read(); "
+            "assert 'libwoodelf' not in maps, 'CUDA library mapped'; "
+            "assert 'liboracle' in maps; print('ok')")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stderr[-2000:]
