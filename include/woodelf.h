@@ -207,9 +207,11 @@ wdf_status wdf_global_attribution(wdf_ctx *ctx, const float *phi, int64_t n, int
  * Ragged batches (project addition; the paper runs one tree ensemble at a time).
  * A batch groups ensembles of one context -- any depths 2..8 and feature counts -- so a
  * single call explains many requests against them with ONE CUDA-graph launch: the graph
- * copies a packed work description (one memcpy) and runs a persistent consumer kernel
- * per depth class on parallel branches over (ensemble, request, tile of consumer rows)
- * work items.  Per-row results equal those of wdf_explain bit for bit.
+ * copies a packed work description (one memcpy) and runs, per depth class on parallel
+ * branches, an encode kernel (the requests' decision codes into a device arena the
+ * batch keeps and grows as needed) and a persistent consumer kernel over (ensemble,
+ * request, tile of consumer rows) work items.  Per-row results equal those of
+ * wdf_explain bit for bit.
  *
  * wdf_batch_create: the ensembles must outlive the batch; their backgrounds may be set
  * (or reset) later but before wdf_batch_explain.

@@ -3,10 +3,11 @@
 //
 // Ensembles are grouped into depth classes (one kernel instantiation per depth).  A
 // call writes every class's work description -- the ensembles' device arrays (jobs),
-// the requests, and the work items (job, request, first row) of tile_rows consumer rows
-// each -- into one pinned host blob; the captured graph copies that blob to the device
-// with a single memcpy and then runs one persistent k_explain_batch per class on
-// parallel branches.  The item count is read on the device, so the same graph serves
+// the requests, the encode items (request, 32-row block) and the work items (job,
+// request, first row) of tile_rows consumer rows each -- into one pinned host blob; the
+// captured graph copies that blob to the device with a single memcpy and then runs, per
+// class on parallel branches, k_encode_batch (the rows' decision codes into the batch's
+// code arena) and one persistent k_explain_batch.  The item count is read on the device, so the same graph serves
 // every call until a capacity grows.  Results per consumer row are exactly those of
 // wdf_explain: the per-row arithmetic and its order do not depend on the batch.
 //
@@ -42,9 +43,13 @@ wdf_status fail(wdf_status s, const std::string &msg) {
 struct Cls {
     int D = 0, F_max = 0, xb_max = 0, tile_rows = 0;
     std::vector<int> members;  // batch ensemble indices, in job-slot order
-    int cap_reqs = 0, cap_items = 0;
-    size_t off_jobs = 0, off_reqs = 0, off_items = 0, off_count = 0;
+    int cap_reqs = 0, cap_items = 0, cap_eitems = 0;
+    size_t off_jobs = 0, off_reqs = 0, off_items = 0, off_count = 0, off_eitems = 0, off_ecount = 0;
 };
+
+// Rows of a request's code region: a multiple of every tile size (and of 32).
+constexpr int64_t kCodePad = 128;
+int64_t padded_rows(int64_t n) { return (n + kCodePad - 1) / kCodePad * kCodePad; }
 
 }  // namespace
 
@@ -62,6 +67,8 @@ struct wdf_batch {
     cudaEvent_t ev_fork = nullptr, ev_copied = nullptr;
     std::vector<cudaEvent_t> ev_join;
     bool copied_pending = false;
+    unsigned char *d_codes = nullptr;  // decision codes of the requests' rows
+    size_t codes_cap = 0;
 };
 
 namespace {
@@ -71,6 +78,7 @@ struct Req {
     const float *C;
     float *phi;
     int64_t n, ldc, ldp;
+    size_t codes_off = 0;  // the request's region of the code arena
 };
 
 void drop_graph(wdf_batch *b) {
@@ -86,11 +94,38 @@ wdf_status wait_copied(wdf_batch *b) {
     return WDF_OK;
 }
 
+// Code arena regions of the requests (one per request, padded rows x the ensemble's code
+// bytes per row), growing the arena if needed.  The regions' addresses travel in the
+// blob, so the captured graph stays valid when the arena moves.
+wdf_status place_codes(wdf_batch *b, std::vector<Req> *reqs) {
+    size_t total = 0;
+    for (Req &r : *reqs) {
+        const wdf::Packed &p = b->ens[(size_t)r.e]->pk;
+        r.codes_off = total;
+        total += (size_t)padded_rows(r.n) * p.cols.size() * (size_t)p.code_bytes;
+    }
+    if (total > b->codes_cap) {
+        wdf_status s = wait_copied(b);
+        if (s != WDF_OK) return s;
+        WDF_CUDA(cudaDeviceSynchronize());  // earlier launches may still read the old arena
+        if (b->d_codes) cudaFree(b->d_codes);
+        b->d_codes = nullptr;
+        b->codes_cap = 0;
+        const size_t cap = std::max<size_t>(total + total / 2, 1 << 20);
+        WDF_CUDA(cudaMalloc((void **)&b->d_codes, cap));
+        b->codes_cap = cap;
+    }
+    return WDF_OK;
+}
+
 // Blob layout for the current capacities; reallocates (and drops the graph) if it grew.
-wdf_status ensure_blob(wdf_batch *b, const std::vector<int> &need_reqs, const std::vector<int> &need_items) {
+wdf_status ensure_blob(wdf_batch *b, const std::vector<int> &need_reqs, const std::vector<int> &need_items,
+                       const std::vector<int> &need_eitems) {
     bool grow = b->h_blob == nullptr;
     for (size_t c = 0; c < b->cls.size(); ++c)
-        if (need_reqs[c] > b->cls[c].cap_reqs || need_items[c] > b->cls[c].cap_items) grow = true;
+        if (need_reqs[c] > b->cls[c].cap_reqs || need_items[c] > b->cls[c].cap_items ||
+            need_eitems[c] > b->cls[c].cap_eitems)
+            grow = true;
     if (!grow) return WDF_OK;
     wdf_status s = wait_copied(b);
     if (s != WDF_OK) return s;
@@ -101,6 +136,7 @@ wdf_status ensure_blob(wdf_batch *b, const std::vector<int> &need_reqs, const st
         Cls &k = b->cls[c];
         k.cap_reqs = std::max(k.cap_reqs, std::max(need_reqs[c], 4) * 3 / 2);
         k.cap_items = std::max(k.cap_items, std::max(need_items[c], 64) * 3 / 2);
+        k.cap_eitems = std::max(k.cap_eitems, std::max(need_eitems[c], 64) * 3 / 2);
         k.off_jobs = off;
         off = up16(off + k.members.size() * sizeof(wdf::ExplainJob));
         k.off_reqs = off;
@@ -108,6 +144,10 @@ wdf_status ensure_blob(wdf_batch *b, const std::vector<int> &need_reqs, const st
         k.off_items = off;
         off = up16(off + (size_t)k.cap_items * sizeof(int4));
         k.off_count = off;
+        off = up16(off + 2 * sizeof(int));
+        k.off_eitems = off;
+        off = up16(off + (size_t)k.cap_eitems * sizeof(int2));
+        k.off_ecount = off;
         off = up16(off + sizeof(int));
     }
     if (b->h_blob) cudaFreeHost(b->h_blob);
@@ -128,12 +168,14 @@ int fill_class(wdf_batch *b, int c, const std::vector<Req> &reqs, int tile_rows)
     for (size_t j = 0; j < k.members.size(); ++j) jobs[j] = b->ens[(size_t)k.members[j]]->job();
     auto *rq = reinterpret_cast<wdf::BatchRequest *>(b->h_blob + k.off_reqs);
     auto *items = reinterpret_cast<int4 *>(b->h_blob + k.off_items);
-    int nr = 0, ni = 0;
+    auto *eitems = reinterpret_cast<int2 *>(b->h_blob + k.off_eitems);
+    int nr = 0, ni = 0, ne = 0;
     for (const Req &r : reqs) {
         if (b->cls_of[(size_t)r.e] != c) continue;
-        rq[nr] = wdf::BatchRequest{r.C, r.phi, r.n, r.ldc, r.ldp};
+        rq[nr] = wdf::BatchRequest{r.C, r.phi, b->d_codes + r.codes_off, r.n, r.ldc, r.ldp, b->slot_of[(size_t)r.e]};
         for (int64_t c0 = 0; c0 < r.n; c0 += tile_rows)
             items[ni++] = make_int4(b->slot_of[(size_t)r.e], nr, (int)(c0 >> 31), (int)(c0 & 0x7FFFFFFF));
+        for (int64_t blk = 0; blk < padded_rows(r.n) / 32; ++blk) eitems[ne++] = make_int2(nr, (int)blk);
         ++nr;
     }
     // longest first: tiles of ensembles with more trees cost more; blocks claim items in
@@ -144,8 +186,12 @@ int fill_class(wdf_batch *b, int c, const std::vector<Req> &reqs, int tile_rows)
     int *hdr = reinterpret_cast<int *>(b->h_blob + k.off_count);
     hdr[0] = ni;  // item count
     hdr[1] = 0;   // claim counter, zero at every launch
+    *reinterpret_cast<int *>(b->h_blob + k.off_ecount) = ne;
     return ni;
 }
+
+// Blocks of the batched encode: eight per SM walk the (request, 32-row block) items.
+int kEncodeGrid(const wdf_batch *b) { return 8 * std::max(1, b->ctx->dev.sms); }
 
 wdf_status capture(wdf_batch *b) {
     drop_graph(b);
@@ -158,6 +204,12 @@ wdf_status capture(wdf_batch *b) {
         const Cls &k = b->cls[c];
         e = cudaStreamWaitEvent(b->branch[c], b->ev_fork, 0);
         if (e == cudaSuccess)
+            e = wdf::launch_encode_batch(reinterpret_cast<const wdf::ExplainJob *>(b->d_blob + k.off_jobs),
+                                         reinterpret_cast<const wdf::BatchRequest *>(b->d_blob + k.off_reqs),
+                                         reinterpret_cast<const int2 *>(b->d_blob + k.off_eitems),
+                                         reinterpret_cast<const int *>(b->d_blob + k.off_ecount), kEncodeGrid(b),
+                                         b->branch[c]);
+        if (e == cudaSuccess)
             e = wdf::launch_explain_batch(
                 k.D, reinterpret_cast<const wdf::ExplainJob *>(b->d_blob + k.off_jobs),
                 reinterpret_cast<const wdf::BatchRequest *>(b->d_blob + k.off_reqs),
@@ -169,7 +221,7 @@ wdf_status capture(wdf_batch *b) {
     }
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
-    wdf::count_launches(-(int)b->cls.size());  // counted per graph launch instead
+    wdf::count_launches(-2 * (int)b->cls.size());  // counted per graph launch instead
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return fail(WDF_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
@@ -197,13 +249,15 @@ wdf_status gather_requests(wdf_batch *b, int32_t nreq, const int32_t *idx, const
 }
 
 void count_needs(const wdf_batch *b, const std::vector<Req> &reqs, const std::vector<int> &tile_rows,
-                 std::vector<int> *need_reqs, std::vector<int> *need_items) {
+                 std::vector<int> *need_reqs, std::vector<int> *need_items, std::vector<int> *need_eitems) {
     need_reqs->assign(b->cls.size(), 0);
     need_items->assign(b->cls.size(), 0);
+    need_eitems->assign(b->cls.size(), 0);
     for (const Req &r : reqs) {
         const int c = b->cls_of[(size_t)r.e];
         (*need_reqs)[(size_t)c] += 1;
         (*need_items)[(size_t)c] += (int)((r.n + tile_rows[(size_t)c] - 1) / tile_rows[(size_t)c]);
+        (*need_eitems)[(size_t)c] += (int)(padded_rows(r.n) / 32);
     }
 }
 
@@ -274,6 +328,7 @@ void wdf_batch_destroy(wdf_batch *b) {
     drop_graph(b);
     if (b->h_blob) cudaFreeHost(b->h_blob);
     if (b->d_blob) cudaFree(b->d_blob);
+    if (b->d_codes) cudaFree(b->d_codes);
     for (cudaStream_t s : b->branch)
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t ev : b->ev_join)
@@ -295,10 +350,11 @@ wdf_status wdf_batch_explain(wdf_batch *b, int32_t n_requests, const int32_t *en
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != b->ctx->device) cudaSetDevice(b->ctx->device);
-    std::vector<int> tiles, need_reqs, need_items;
+    std::vector<int> tiles, need_reqs, need_items, need_eitems;
     for (const Cls &k : b->cls) tiles.push_back(k.tile_rows);
-    count_needs(b, reqs, tiles, &need_reqs, &need_items);
-    s = ensure_blob(b, need_reqs, need_items);
+    count_needs(b, reqs, tiles, &need_reqs, &need_items, &need_eitems);
+    s = ensure_blob(b, need_reqs, need_items, need_eitems);
+    if (s == WDF_OK) s = place_codes(b, &reqs);
     if (s == WDF_OK) s = wait_copied(b);
     if (s == WDF_OK) {
         for (size_t c = 0; c < b->cls.size(); ++c) fill_class(b, (int)c, reqs, b->cls[c].tile_rows);
@@ -309,7 +365,7 @@ wdf_status wdf_batch_explain(wdf_batch *b, int32_t n_requests, const int32_t *en
         if (e != cudaSuccess) s = fail(WDF_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
         else {
             b->copied_pending = true;
-            wdf::count_launches((int)b->cls.size());
+            wdf::count_launches(2 * (int)b->cls.size());
         }
     }
     if (prev >= 0 && prev != b->ctx->device) cudaSetDevice(prev);
@@ -340,9 +396,10 @@ wdf_status wdf_batch_autotune(wdf_batch *b, int32_t n_requests, const int32_t *e
     if (prev != b->ctx->device) cudaSetDevice(b->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int cand[3] = {32, 64, 128};
-    std::vector<int> t32(b->cls.size(), 32), need_reqs, need_items;
-    count_needs(b, reqs, t32, &need_reqs, &need_items);  // tile_rows 32 needs the most items
-    s = ensure_blob(b, need_reqs, need_items);
+    std::vector<int> t32(b->cls.size(), 32), need_reqs, need_items, need_eitems;
+    count_needs(b, reqs, t32, &need_reqs, &need_items, &need_eitems);  // tile_rows 32 needs the most items
+    s = ensure_blob(b, need_reqs, need_items, need_eitems);
+    if (s == WDF_OK) s = place_codes(b, &reqs);
     if (s == WDF_OK) s = wait_copied(b);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (s == WDF_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
@@ -362,6 +419,21 @@ wdf_status wdf_batch_autotune(wdf_batch *b, int32_t n_requests, const int32_t *e
         }
         float best_ms = 1e30f;
         int best = k.tile_rows;
+        // the rows' codes do not depend on the tile size: encode them once
+        fill_class(b, (int)c, reqs, k.tile_rows);
+        {
+            cudaError_t e = cudaMemcpyAsync(b->d_blob, b->h_blob, b->blob_bytes, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = wdf::launch_encode_batch(reinterpret_cast<const wdf::ExplainJob *>(b->d_blob + k.off_jobs),
+                                             reinterpret_cast<const wdf::BatchRequest *>(b->d_blob + k.off_reqs),
+                                             reinterpret_cast<const int2 *>(b->d_blob + k.off_eitems),
+                                             reinterpret_cast<const int *>(b->d_blob + k.off_ecount), kEncodeGrid(b),
+                                             st);
+            if (e != cudaSuccess) {
+                s = fail(WDF_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+                break;
+            }
+        }
         for (int tc : cand) {
             if (wdf::explain_smem_bytes(k.D, k.F_max, k.xb_max, tc) > b->ctx->dev.smem_optin) continue;
             fill_class(b, (int)c, reqs, tc);

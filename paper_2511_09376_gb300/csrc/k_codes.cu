@@ -14,15 +14,17 @@ namespace wdf {
 constexpr int kEncodeThreads = 256;
 constexpr int kEncodeCols = 128;  // 16.5 KB of staging: fits beside a counting block
 
-__global__ void __launch_bounds__(kEncodeThreads) k_encode_codes(const float *__restrict__ X, int64_t rows,
-                                                                int64_t ldx, TreeArrays ta,
-                                                                unsigned char *__restrict__ codes) {
-    __shared__ float xs[32 * (kEncodeCols + 1)];
+// Code block `block` (rows 32 block .. 32 block + 31) of rows [0, rows) of X, written at
+// codes + block * n_cols * 32 * code bytes.  xs: 32 x (kEncodeCols + 1) floats of shared
+// memory.  All threads of the block call it.
+__device__ __forceinline__ void encode_block(const float *__restrict__ X, int64_t rows, int64_t ldx,
+                                             const TreeArrays &ta, int64_t block, unsigned char *__restrict__ codes,
+                                             float *xs) {
     const int ncol = ta.n_cols, cb = ta.code_bytes;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t row0 = (int64_t)blockIdx.x * 32;
+    const int64_t row0 = block * 32;
     const bool valid = row0 + lane < rows;
-    unsigned char *dst = codes + (size_t)blockIdx.x * ncol * 32 * cb;
+    unsigned char *dst = codes + (size_t)block * ncol * 32 * cb;
     for (int c0 = 0; c0 < ncol; c0 += kEncodeCols) {
         const int cn = min(kEncodeCols, ncol - c0);
         __syncthreads();
@@ -54,6 +56,35 @@ __global__ void __launch_bounds__(kEncodeThreads) k_encode_codes(const float *__
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(kEncodeThreads) k_encode_codes(const float *__restrict__ X, int64_t rows,
+                                                                int64_t ldx, TreeArrays ta,
+                                                                unsigned char *__restrict__ codes) {
+    __shared__ float xs[32 * (kEncodeCols + 1)];
+    encode_block(X, rows, ldx, ta, blockIdx.x, codes, xs);
+}
+
+// The rows of a ragged batch: item i = (request, 32-row block); blocks walk the items.
+__global__ void __launch_bounds__(kEncodeThreads) k_encode_batch(const ExplainJob *__restrict__ jobs,
+                                                                const BatchRequest *__restrict__ reqs,
+                                                                const int2 *__restrict__ items,
+                                                                const int *__restrict__ n_items) {
+    __shared__ float xs[32 * (kEncodeCols + 1)];
+    const int count = n_items[0];
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const int2 it = items[i];
+        const BatchRequest rq = reqs[it.x];
+        const TreeArrays ta = jobs[rq.job].ta;
+        encode_block(rq.C, rq.n, rq.ldc, ta, it.y, rq.codes, xs);
+    }
+}
+
+cudaError_t launch_encode_batch(const ExplainJob *jobs, const BatchRequest *reqs, const int2 *items,
+                                const int *n_items, int grid, cudaStream_t st) {
+    k_encode_batch<<<grid, kEncodeThreads, 0, st>>>(jobs, reqs, items, n_items);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_encode_codes(const float *X, int64_t rows, int64_t ldx, const TreeArrays &ta, int64_t rows_pad,

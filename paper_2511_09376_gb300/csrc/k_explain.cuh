@@ -109,88 +109,15 @@ __device__ __forceinline__ void load_offsets8(const int *p, int (&o)[8]) {
     o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
 }
 
-// Decision codes (tree_layout.h) of the tile's rows, written into the code tile sx in
-// 32-row code blocks.  The rows are first staged in the phi region (free until the tree
-// loop), TC rows of FS floats (FS = F rounded up to odd, so that the lanes of a warp,
-// one row each, read different banks); then warp w encodes code block w, lane = row,
-// one binary search per code column, sixteen columns in flight so their dependent
-// threshold loads overlap.  A row past n gets code 0 (its phi is never written).
-template <int TC>
-__device__ __forceinline__ void encode_tile(const float *__restrict__ C, int64_t n, int64_t ldc, int64_t c0,
-                                            const TreeArrays &ta, int F, float *stage, unsigned char *sx, int tid) {
-    constexpr int IL = 16;  // searches in flight per thread: their threshold loads are mostly L2 round trips
-    const int FS = F | 1;
-    const int rows = (int)min((int64_t)TC, n - c0);
-    // every element of the tile in flight at once (asynchronous 4-byte copies; the rows
-    // come from HBM, so element-by-element loads would serialise their latency)
-    for (int r = tid / 32; r < TC; r += TC / 32) {
-        const float *src = C + (c0 + r) * ldc;
-        for (int f = tid & 31; f < F; f += 32) {
-            float *dst = stage + r * FS + f;
-            if (r < rows)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                                 static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-                             "l"(src + f)
-                             : "memory");
-            else
-                *dst = 0.0f;
-        }
-    }
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
-    const int lane = tid & 31, warp = tid >> 5, row = warp * 32 + lane;
-    const bool valid = row < rows;
-    const float *xr = stage + row * FS;
-    const int ncol = ta.n_cols, cb = ta.code_bytes;
-    unsigned char *dst = sx + (size_t)warp * 32 * ncol * cb;
-    const int4 *cols = reinterpret_cast<const int4 *>(ta.cols);
-    if (cb == 1) {
-        // one-byte columns hold 255 thresholds padded with NaN (never <= x): a search from
-        // the column's top power of two needs no bound checks; NaN x gets the count
-        for (int cc = 0; cc < ncol; cc += IL) {
-            float x[IL];
-            int pos[IL], top[IL], first[IL];
-#pragma unroll
-            for (int j = 0; j < IL; ++j) {
-                const int4 cv = cc + j < ncol ? __ldg(cols + cc + j) : make_int4(0, 0, 0, 0);
-                x[j] = xr[cv.x];
-                first[j] = cv.y;
-                top[j] = cv.w;
-                pos[j] = x[j] != x[j] ? -cv.z - 1 : 0;  // NaN: the count, kept out of the search
-            }
-#pragma unroll
-            for (int step = 128; step > 0; step >>= 1) {
-#pragma unroll
-                for (int j = 0; j < IL; ++j)
-                    if (step <= top[j] && pos[j] >= 0)
-                        pos[j] += __ldg(ta.col_thr + first[j] + pos[j] + step - 1) <= x[j] ? step : 0;
-            }
-#pragma unroll
-            for (int j = 0; j < IL; ++j)
-                if (cc + j < ncol)
-                    dst[(cc + j) * 32 + lane] = (unsigned char)(!valid ? 0 : (pos[j] < 0 ? -pos[j] - 1 : pos[j]));
-        }
-    } else {
-        for (int c = 0; c < ncol; ++c) {
-            const int4 cv = __ldg(cols + c);
-            const int code = valid ? decision_code(xr[cv.x], ta.col_thr + cv.y, CodeCol{cv.x, cv.y, cv.z, cv.w}) : 0;
-            reinterpret_cast<uint16_t *>(dst)[c * 32 + lane] = (uint16_t)code;
-        }
-    }
-    __syncthreads();
-}
-
-// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble.  ENC:
-// the rows' decision codes are computed here from C (encode_tile); otherwise they are
-// copied from codes, the code blocks of all n rows written by k_encode_codes (padded
-// to a multiple of TC rows).  The plain path encodes in a kernel of its own: in-tile
-// encoding measured 1.9 ms per 1M rows slower at the large workload (ten warps per SM
-// cannot hide the dependent threshold loads of the searches), so only the ragged batch,
-// whose rows arrive in one graph launch, encodes in the tile.
-template <int D, int TC, bool ENC>
-__device__ __forceinline__ void explain_tile(const ExplainJob &job, const float *__restrict__ C, int64_t n,
-                                             int64_t ldc, const unsigned char *__restrict__ codes,
-                                             float *__restrict__ phi, int64_t ldp, int64_t c0,
+// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble.  The
+// rows' decision codes are copied from codes, the code blocks of all n rows written by
+// k_encode_codes or k_encode_batch (padded to a multiple of TC rows).  Encoding inside
+// the tile measured 1.9 ms per 1M rows slower at the large workload: ten warps per SM
+// cannot hide the dependent threshold loads of the searches, which the encode kernels
+// run at full occupancy.
+template <int D, int TC>
+__device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsigned char *__restrict__ codes,
+                                             int64_t n, float *__restrict__ phi, int64_t ldp, int64_t c0,
                                              unsigned char *smem_raw) {
     using S = Shape<D>;
     using X = ExplainCfg<D>;
@@ -210,9 +137,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const float 
     int4 *srec = reinterpret_cast<int4 *>(smem_raw + L.x + L.p + L.meta);
     int *sfl = reinterpret_cast<int *>(smem_raw + L.x + L.p + L.meta + L.rec);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if constexpr (ENC) {
-        encode_tile<TC>(C, n, ldc, c0, ta, F, sp, sx, tid);
-    } else {
+    {
         const uint4 *src = reinterpret_cast<const uint4 *>(codes + c0 * xb);
         for (int i = tid; i < TC * xb / 16; i += TC) reinterpret_cast<uint4 *>(sx)[i] = __ldg(src + i);
     }
@@ -342,7 +267,7 @@ template <int D, int TC>
 __global__ void __launch_bounds__(TC, 1) k_explain(const unsigned char *__restrict__ codes, int64_t n,
                                                    ExplainJob job, float *__restrict__ phi, int64_t ldp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    explain_tile<D, TC, false>(job, nullptr, n, 0, codes, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
+    explain_tile<D, TC>(job, codes, n, phi, ldp, (int64_t)blockIdx.x * TC, smem_raw);
 }
 
 // Persistent form over a ragged batch: work item i is (job, request, first row).  Blocks
@@ -367,7 +292,7 @@ __global__ void __launch_bounds__(TC, 1) k_explain_batch(const ExplainJob *__res
         const ExplainJob job = jobs[it.x];
         const BatchRequest rq = reqs[it.y];
         const int64_t c0 = ((int64_t)it.z << 31) | (uint32_t)it.w;
-        explain_tile<D, TC, true>(job, rq.C, rq.n, rq.ldc, nullptr, rq.phi, rq.ldp, c0, smem_raw);
+        explain_tile<D, TC>(job, rq.codes, rq.n, rq.phi, rq.ldp, c0, smem_raw);
         __syncthreads();
     }
 }

@@ -47,11 +47,15 @@ __host__ __device__ __forceinline__ uint32_t line_pos(uint32_t e, uint32_t r, in
 // so that a tree's maps are whole 16-byte loads.
 __host__ __device__ constexpr int lines_words(int D) { return (1 << (D - 2)) / 4 < 4 ? 4 : (1 << (D - 2)) / 4; }
 
-// One request of a ragged batch: n consumer rows at C (row stride ldc), phi out.
+// One request of a ragged batch: n consumer rows at C (row stride ldc), phi out; codes
+// receives the rows' decision code blocks (rows padded to a multiple of 128), job is
+// the slot of the request's ensemble among its class's jobs.
 struct BatchRequest {
     const float *C;
     float *phi;
+    unsigned char *codes;
     int64_t n, ldc, ldp;
+    int job;
 };
 
 struct DevInfo {
@@ -150,9 +154,14 @@ cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const 
 int default_tile_rows(int D, int F, int xb, const DevInfo &dev);
 size_t explain_smem_bytes(int D, int F, int xb, int tile_rows);
 
+// Decision codes of a ragged batch's rows: items (request, 32-row block), *n_items read on
+// the device; a grid of `grid` blocks walks them.
+cudaError_t launch_encode_batch(const ExplainJob *jobs, const BatchRequest *reqs, const int2 *items,
+                                const int *n_items, int grid, cudaStream_t st);
+
 // Step 4 for a ragged batch of one depth: a persistent grid (grid <= 0: one wave at full
 // occupancy) walks the work items (job, request, first row split as hi/lo words);
-// *n_items is read on the device.  F_max and xb_max bound the feature count and the
+// *n_items is read on the device; the rows' codes come from launch_encode_batch.  F_max and xb_max bound the feature count and the
 // decision-code bytes per row of every job.
 cudaError_t launch_explain_batch(int D, const ExplainJob *jobs, const BatchRequest *reqs, const int4 *items,
                                  int *n_items, int F_max, int xb_max, int tile_rows, int grid, const DevInfo &dev,
