@@ -867,6 +867,39 @@ def contraction_compare(args) -> dict:
     return out
 
 
+def run_deep(args):
+    """--workload deep: the plain path (one wdf_explain of device rows) on the 1000-tree
+    depth-8 serving ensemble, the one whose largest requests set the serving p99."""
+    import torch
+
+    import paper_2511_09376_gb300 as wdf
+    from paper_2511_09376_gb300 import synth
+    w = synth.serving_specs()[3]
+    n = args.consumers or 100_000
+    e_np, _, B = synth.make(w, n_background=args.background)
+    ctx = wdf.ctx_create(0)
+    e = wdf.load_ensemble(ctx, e_np)
+    wdf.set_background(e, torch.from_numpy(B).cuda(), SPLIT_BF16)
+    C = torch.from_numpy(synth.consumers(w, n)).cuda()
+    phi = torch.empty_like(C)
+    for _ in range(args.warmup):
+        wdf.explain(e, C, out=phi)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        wdf.explain(e, C, out=phi)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    return {"metric": METRIC, "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"deep: the plain path on the serving ensemble of {w.n_trees} trees of depth "
+                                   f"{w.depth} (F={w.n_features}), n={n} device rows, background of "
+                                   f"{B.shape[0]} rows ({SPLIT_BF16} contraction)"}}
+
+
 def run_ragged(args):
     """--workload ragged: the ragged comparison as the JSON line (value = batched rows/s)."""
     r = ragged_compare(args)
@@ -922,6 +955,9 @@ def main():
         return
     if args.workload == "serving":
         print(json.dumps(run_serving(args)), flush=True)
+        return
+    if args.workload == "deep":
+        print(json.dumps(run_deep(args)), flush=True)
         return
     if args.workload == "contraction":
         print(json.dumps({"contraction": contraction_compare(args)}), flush=True)
