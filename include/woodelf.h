@@ -264,7 +264,9 @@ wdf_status wdf_batch_tile_rows(const wdf_batch *batch, int32_t depth, int32_t *t
  * request; WDF_EINVAL for an unknown or unfinished ticket.
  * wdf_server_stats: latency percentiles are over requests completed since creation or
  * the last wdf_server_reset_stats, measured from submit to completion; rows_per_s over
- * the span from the first submit to the last completion.  wdf_server_destroy finishes
+ * the span from the first submit to the last completion.  wdf_server_reset_stats also
+ * forgets the tickets of completed requests (later waits, polls and latency queries on
+ * them return WDF_EINVAL), which keeps a long-running server's bookkeeping bounded.  wdf_server_destroy finishes
  * every queued request first.
  */
 typedef struct wdf_server wdf_server;

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.h"
 #include "wdf_internal.h"
 #include "woodelf.h"
@@ -73,6 +75,8 @@ std::atomic<int64_t> g_launches{0};
 namespace wdf {
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 void set_last_error(const std::string &msg) { g_err = msg; }
+TraceRange::TraceRange(const char *name) { nvtxRangePushA(name); }
+TraceRange::~TraceRange() { nvtxRangePop(); }
 }  // namespace wdf
 
 #include "wdf_objects.h"
@@ -320,6 +324,7 @@ void wdf_ctx_destroy(wdf_ctx *ctx) { delete ctx; }
 wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, const int64_t *tree_offset,
                              const int32_t *feature, const float *threshold, const int32_t *left,
                              const int32_t *right, const float *value, wdf_ensemble **out) {
+    wdf::TraceRange trace_("wdf_load_ensemble");
     if (!ctx || !out) return fail(WDF_EINVAL, "ctx and out must be non-null");
     *out = nullptr;
     wdf_ensemble *e = new wdf_ensemble();
@@ -430,6 +435,7 @@ wdf_status wdf_set_metric(wdf_ensemble *ens, wdf_metric metric) {
 
 wdf_status wdf_set_background(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, wdf_memkind kind,
                               wdf_precision precision, void *stream) {
+    wdf::TraceRange trace_("wdf_set_background");
     if (!ens) return fail(WDF_EINVAL, "ens is null");
     if (m == 0) return fail(WDF_EUNSUPPORTED, "empty background (m == 0)");
     if (m < 0 || !B) return fail(WDF_EINVAL, "m must be positive and B non-null");
@@ -483,6 +489,7 @@ int64_t wdf_background_counts_size(const wdf_ensemble *ens) {
 
 wdf_status wdf_background_counts(wdf_ensemble *ens, const float *B, int64_t m, int64_t ldb, uint32_t *counts,
                                  void *stream) {
+    wdf::TraceRange trace_("wdf_background_counts");
     if (!ens) return fail(WDF_EINVAL, "ens is null");
     if (m < 0) return fail(WDF_EINVAL, "m < 0");
     if (m == 0) return WDF_OK;
@@ -498,6 +505,7 @@ wdf_status wdf_background_counts(wdf_ensemble *ens, const float *B, int64_t m, i
 
 wdf_status wdf_set_background_counts(wdf_ensemble *ens, const uint32_t *counts, int64_t m_total,
                                      wdf_precision precision, void *stream) {
+    wdf::TraceRange trace_("wdf_set_background_counts");
     if (!ens) return fail(WDF_EINVAL, "ens is null");
     if (!counts) return fail(WDF_EINVAL, "counts is null");
     if (m_total < 1) return fail(WDF_EUNSUPPORTED, "empty background (m_total < 1)");
@@ -528,6 +536,7 @@ wdf_status wdf_set_covers(wdf_ensemble *ens, const double *cover) {
 }
 
 wdf_status wdf_set_path_dependent(wdf_ensemble *ens, wdf_precision precision, void *stream) {
+    wdf::TraceRange trace_("wdf_set_path_dependent");
     if (!ens) return fail(WDF_EINVAL, "ens is null");
     if (!ens->has_covers) return fail(WDF_EINVAL, "wdf_set_covers must succeed before wdf_set_path_dependent");
     if (!valid_precision(precision))
@@ -551,6 +560,7 @@ wdf_status wdf_set_path_dependent(wdf_ensemble *ens, wdf_precision precision, vo
 
 wdf_status wdf_explain(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc, wdf_memkind kind, float *phi,
                        int64_t ldphi, void *stream) {
+    wdf::TraceRange trace_("wdf_explain");
     if (!ens) return fail(WDF_EINVAL, "ens is null");
     if (!ens->has_bg) return fail(WDF_EINVAL, "wdf_set_background must succeed before wdf_explain");
     if (n < 0) return fail(WDF_EINVAL, "n < 0");
@@ -589,6 +599,7 @@ wdf_status wdf_explain(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc
 
 wdf_status wdf_explain_interactions(wdf_ensemble *ens, const float *C, int64_t n, int64_t ldc, float *out,
                                     int64_t ldo, void *stream) {
+    wdf::TraceRange trace_("wdf_explain_interactions");
     if (!ens) return fail(WDF_EINVAL, "ens is null");
     if (!ens->has_bg)
         return fail(WDF_EINVAL, "wdf_set_background or wdf_set_path_dependent must succeed before interactions");
@@ -636,6 +647,7 @@ wdf_status wdf_expected_value(const wdf_ensemble *ens, double *out, void *stream
 
 wdf_status wdf_global_attribution(wdf_ctx *ctx, const float *phi, int64_t n, int64_t ldphi, int32_t n_features,
                                   double *mean_abs, double *mean, void *stream) {
+    wdf::TraceRange trace_("wdf_global_attribution");
     if (!ctx || !mean_abs || !mean) return fail(WDF_EINVAL, "null argument");
     if (n < 0 || n_features < 1 || ldphi < n_features) return fail(WDF_EINVAL, "bad sizes");
     if (n > 0 && !phi) return fail(WDF_EINVAL, "phi is null");

@@ -343,6 +343,7 @@ void wdf_batch_destroy(wdf_batch *b) {
 wdf_status wdf_batch_explain(wdf_batch *b, int32_t n_requests, const int32_t *ensemble_index, const float *const *C,
                              const int64_t *n, const int64_t *ldc, float *const *phi, const int64_t *ldphi,
                              void *stream) {
+    wdf::TraceRange trace_("wdf_batch_explain");
     if (!b) return fail(WDF_EINVAL, "batch is null");
     std::vector<Req> reqs;
     wdf_status s = gather_requests(b, n_requests, ensemble_index, C, n, ldc, phi, ldphi, &reqs);
@@ -375,6 +376,7 @@ wdf_status wdf_batch_explain(wdf_batch *b, int32_t n_requests, const int32_t *en
 wdf_status wdf_batch_autotune(wdf_batch *b, int32_t n_requests, const int32_t *ensemble_index, const float *const *C,
                               const int64_t *n, const int64_t *ldc, float *const *phi, const int64_t *ldphi,
                               int32_t reps, const char *cache_path, void *stream) {
+    wdf::TraceRange trace_("wdf_batch_autotune");
     if (!b) return fail(WDF_EINVAL, "batch is null");
     std::vector<Req> reqs;
     wdf_status s = gather_requests(b, n_requests, ensemble_index, C, n, ldc, phi, ldphi, &reqs);

@@ -18,6 +18,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <iterator>
 #include <map>
 #include <mutex>
 #include <string>
@@ -115,6 +116,7 @@ void run(wdf_server *s);
 // host buffers.  recorded is false only if even the event could not be recorded; the
 // stream has then been synchronised before returning.
 cudaError_t launch_wave(wdf_server *s, Wave &w, bool *recorded) {
+    wdf::TraceRange trace_("wdf_server wave");
     cudaStream_t st = s->stream[(size_t)w.slot];
     std::vector<int32_t> idx;
     std::vector<const float *> C;
@@ -459,6 +461,10 @@ wdf_status wdf_server_reset_stats(wdf_server *s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->lat_ms.clear();
     s->submitted = s->completed = s->rows_done = s->waves = 0;
+    // completed tickets are forgotten, so a long-running server's bookkeeping stays bounded
+    for (auto it = s->state.begin(); it != s->state.end();)
+        it = it->second >= 2 ? s->state.erase(it) : std::next(it);
+    s->done_ms.clear();
     return WDF_OK;
 }
 

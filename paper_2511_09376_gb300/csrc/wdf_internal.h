@@ -68,6 +68,15 @@ int pack_ensemble(int F, int T, const int64_t *off, const int32_t *feat, const f
 // Sets the thread-local message returned by wdf_last_error.
 void set_last_error(const std::string &msg);
 
+// A named range on the NVTX timeline (Nsight Systems, ncu's range filters) for the
+// duration of one C-ABI call or one server wave; a no-op when no tool is attached.
+struct TraceRange {
+    explicit TraceRange(const char *name);
+    ~TraceRange();
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+
 inline int slot_pad(int D) { return (D + 1) <= 4 ? 4 : ((D + 1) <= 8 ? 8 : 12); }
 
 }  // namespace wdf
