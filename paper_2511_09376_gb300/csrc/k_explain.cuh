@@ -21,6 +21,7 @@
 #pragma once
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include "tree_layout.h"
 #include "launch.h"
@@ -31,14 +32,21 @@ namespace wdf {
 template <int D>
 struct ExplainCfg {
     // trees per shared-memory chunk: two keeps the block small (five blocks of 64 rows
-    // per SM at 127 features), measured faster than eight despite four times the barriers
-    static constexpr int TCH = 2;
-    // bottom subtrees gathered together: the largest power of two (a divisor of NS) whose
-    // slot vectors fit in 128 registers
-    static constexpr int gs(int g) { return (g > 1 && g * Shape<D>::SP > 128) ? gs(g / 2) : g; }
-    static constexpr int GS = gs(Shape<D>::NS);
+    // per SM at 127 features), measured faster than eight despite four times the barriers;
+    // one at depth 8, whose node records would otherwise cost a block per SM (four
+    // instead of three 64-row blocks at 134 features: 25 % faster)
+    static constexpr int TCH = D >= 8 ? 1 : 2;
+    // bottom subtrees gathered together (tree_layout.h); deep trees have several groups
+    static constexpr int GS = gather_group(D);
+    static constexpr int NG = Shape<D>::NS / GS;
     static_assert(Shape<D>::NS % GS == 0, "gather groups must tile the bottom subtrees");
-    static_assert(GS == Shape<D>::NS || (3 * GS) % 8 == 0, "flush batches must not straddle gather groups");
+    // the group loop is unrolled: rolled (group index in a register, its decision fields
+    // and ancestor slots selected at run time) it had no instruction-cache misses at
+    // depth 8 but 13 % more instructions, and measured slower
+    static constexpr int GUNROLL = NG;
+    // phi offsets of the flush positions: 16 bits for deep trees (every offset is below
+    // the 58,112 floats a block's shared memory can hold), 32 bits otherwise
+    using Off = typename std::conditional<(D >= 7), uint16_t, int>::type;
 };
 
 // Shared memory of one block: code tile (TC rows x xb bytes) | phi tile ((F + 1) x (TC + 1)
@@ -53,7 +61,7 @@ struct ExLayout {
         p = up((size_t)(F + 1) * (TC + 1) * 4);
         meta = up((size_t)ExplainCfg<D>::TCH * sizeof(TreeMeta));
         rec = up((size_t)ExplainCfg<D>::TCH * Shape<D>::NI * sizeof(NodeRec));
-        fl = up((size_t)ExplainCfg<D>::TCH * flush_len(D) * sizeof(int));
+        fl = up((size_t)ExplainCfg<D>::TCH * flush_len(D) * sizeof(typename ExplainCfg<D>::Off));
         total = x + p + meta + rec + fl;
     }
 };
@@ -108,8 +116,76 @@ __device__ __forceinline__ void load_offsets8(const int *p, int (&o)[8]) {
     o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
     o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
 }
+__device__ __forceinline__ void load_offsets8(const uint16_t *p, int (&o)[8]) {
+    const uint4 a = *reinterpret_cast<const uint4 *>(p);
+    o[0] = (int)(a.x & 0xFFFFu); o[1] = (int)(a.x >> 16); o[2] = (int)(a.y & 0xFFFFu); o[3] = (int)(a.y >> 16);
+    o[4] = (int)(a.z & 0xFFFFu); o[5] = (int)(a.z >> 16); o[6] = (int)(a.w & 0xFFFFu); o[7] = (int)(a.w >> 16);
+}
 
-// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble.  The
+// phi[offset of flush position i] += val[i] for the N positions that follow fl, in
+// batches of eight (batch b0 first); the next batch's offsets are read before this
+// batch's phi writes, so the offset loads stay off the chain of dependent shared-memory
+// round trips.  A batch of pass-through nodes only is skipped (real), a batch that
+// repeats no feature reads before it writes (fok).
+template <int N, class Off, class Val>
+__device__ __forceinline__ void flush_run(float *myphi, const Off *fl, const Val &value, uint64_t real, uint64_t fok,
+                                          int b0) {
+    int o[8];
+    load_offsets8(fl, o);
+#pragma unroll
+    for (int i0 = 0; i0 < N; i0 += 8) {
+        int on[8];
+        if (i0 + 8 < N) load_offsets8(fl + i0 + 8, on);
+        float vv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) vv[q] = i0 + q < N ? value(i0 + q) : 0.0f;
+        const int b = b0 + i0 / 8;
+        if ((real >> b) & 1u) flush_batch(myphi, o, vv, N - i0 < 8 ? N - i0 : 8, (fok >> b) & 1u);
+        if (i0 + 8 < N) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o[q] = on[q];
+        }
+    }
+}
+
+// Slot k of a gathered slot vector held as Q float4 registers (k a compile-time constant
+// after unrolling; a float pointer into the float4 array kept it in local memory).
+template <int Q>
+__device__ __forceinline__ float slot_of(const float4 (&vj)[Q], int k) {
+    const float4 &x = vj[k >> 2];
+    return (k & 3) == 0 ? x.x : (k & 3) == 1 ? x.y : (k & 3) == 2 ? x.z : x.w;
+}
+
+// Decision bits of tree level l (heap nodes 2^l - 1 .. 2^(l+1) - 2), aligned to the
+// level's first node: word k holds nodes 2^l - 1 + 32k ... (levels of fewer than 32 nodes:
+// one word, high bits beyond the level undefined).
+template <int D, int l>
+struct LevelBits {
+    static constexpr int W = (1 << l) / 32 > 0 ? (1 << l) / 32 : 1;
+    uint32_t w[W];
+    __device__ __forceinline__ explicit LevelBits(const uint32_t (&dw)[Shape<D>::NW]) {
+        constexpr int NW = Shape<D>::NW;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const int s = (1 << l) - 1 + 32 * k, a = s >> 5, sh = s & 31;
+            const uint32_t hi = a + 1 < NW ? dw[a + 1 < NW ? a + 1 : 0] : 0u;
+            w[k] = sh == 0 ? dw[a] : __funnelshift_r(dw[a], hi, sh);
+        }
+    }
+    // the `width` bits of nodes g * width .. g * width + width - 1 of the level (width a
+    // power of two <= 32, so a field never straddles two words)
+    template <int width>
+    __device__ __forceinline__ uint32_t field(int g) const {
+        const uint32_t at = (uint32_t)g * width;
+        uint32_t x = w[0];
+#pragma unroll
+        for (int k = 1; k < W; ++k) x = (at >> 5) == (uint32_t)k ? w[k] : x;
+        if constexpr (width == 32) return x;
+        else return (x >> (at & 31u)) & ((1u << width) - 1u);
+    }
+};
+
+// One tile of TC consumer rows// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble.  The
 // rows' decision codes are copied from codes, the code blocks of all n rows written by
 // k_encode_codes or k_encode_batch (padded to a multiple of TC rows).  Encoding inside
 // the tile measured 1.9 ms per 1M rows slower at the large workload: ten warps per SM
@@ -125,7 +201,8 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
     constexpr int NA = S::NS > 1 ? S::NS - 1 : 1;
     constexpr int GS = X::GS;
     constexpr int Q = S::SP / 4;
-    constexpr int FL = flush_len(D), FLB = flush_len_bottom(D);
+    constexpr int FL = flush_len(D), FLB = flush_group_bottom(D);
+    using Off = typename X::Off;
     const int F = job.F, T = job.T;
     const TreeArrays &ta = job.ta;
     const float *__restrict__ sfold = job.sfold;
@@ -135,7 +212,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
     float *sp = reinterpret_cast<float *>(smem_raw + L.x);
     TreeMeta *smeta = reinterpret_cast<TreeMeta *>(smem_raw + L.x + L.p);
     int4 *srec = reinterpret_cast<int4 *>(smem_raw + L.x + L.p + L.meta);
-    int *sfl = reinterpret_cast<int *>(smem_raw + L.x + L.p + L.meta + L.rec);
+    Off *sfl = reinterpret_cast<Off *>(smem_raw + L.x + L.p + L.meta + L.rec);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(codes + c0 * xb);
@@ -149,106 +226,205 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
         __syncthreads();
         stage_trees<D>(tc0, tcn, ta.rec, ta.meta, srec, smeta, tid, TC);
         // phi offsets of every tree in flush order (padding and pass-through nodes: the
-        // scratch row F)
-        for (int i = tid; i < tcn * FL; i += TC) {
-            const int g = i / FL, v = flush_node(D, i - g * FL);
-            sfl[i] = (v >= 0 ? __ldg(&ta.nodes[(size_t)(tc0 + g) * S::NI + v].x) : F) * XS;
+        // scratch row F), from the features the host lists in flush order.  Depth 8
+        // recomputes the positions here instead: measured 13 % faster at 1000 trees (the
+        // longer staging step changes how the blocks share the instruction cache and L2:
+        // 0.36e9 instead of 0.66e9 instruction-cache misses, L2 hit rate 96 % instead of
+        // 85 %), while depths 6 and 7 are 3-10 % faster with the list.
+        if constexpr (D >= 8) {
+            for (int i = tid; i < tcn * FL; i += TC) {
+                const int g = i / FL, v = flush_node(D, i - g * FL);
+                sfl[i] = (Off)((v >= 0 ? __ldg(&ta.nodes[(size_t)(tc0 + g) * S::NI + v].x) : F) * XS);
+            }
+        } else {
+            for (int i = tid; i < tcn * FL; i += TC) sfl[i] = (Off)(__ldg(job.flfeat + (size_t)tc0 * FL + i) * XS);
         }
         __syncthreads();
         for (int g = 0; g < tcn; ++g) {
             const int t = tc0 + g;
             const TreeMeta &mt = smeta[g];
-            const int *fl = sfl + g * FL;
+            const Off *fl = sfl + g * FL;
             uint32_t dw[S::NW];
             // one generic decision loop for both code widths (a second, one-byte copy in
             // this loop measured slower here, unlike in the counting kernel; node words
             // packed four to a 16-byte load measured slower too: the decoding cost more
             // issue slots than the shared-memory wavefronts it saved)
             tree_decisions<D, false>(srec + g * S::NI, mt, xr, dw);
-            uint32_t ent[S::NS];
-            subtree_entries<D>(dw, ent);
             const uint64_t lv = mt.live;
-            const uint32_t fok = mt.flush, real = mt.real;
             const float4 *tf = reinterpret_cast<const float4 *>(sfold + (size_t)t * S::NS * S::E * S::SP);
-            // the tree's line maps (launch.h), one byte per bottom subtree
             constexpr int LW = lines_words(D);
-            uint32_t lmap[LW];
+            if constexpr (X::NG == 1) {
+                const uint32_t fok = (uint32_t)mt.flush, real = (uint32_t)mt.real;
+                uint32_t ent[S::NS];
+                subtree_entries<D>(dw, ent);
+                // the tree's line maps (launch.h), one byte per bottom subtree
+                uint32_t lmap[LW];
 #pragma unroll
-            for (int w = 0; w < LW; w += 4) {
-                const uint4 v4 = __ldg(reinterpret_cast<const uint4 *>(job.lines + (size_t)t * LW) + w / 4);
-                lmap[w] = v4.x; lmap[w + 1] = v4.y; lmap[w + 2] = v4.z; lmap[w + 3] = v4.w;
-            }
-            float acc[NA];
+                for (int w = 0; w < LW; w += 4) {
+                    const uint4 v4 = __ldg(reinterpret_cast<const uint4 *>(job.lines + (size_t)t * LW) + w / 4);
+                    lmap[w] = v4.x; lmap[w + 1] = v4.y; lmap[w + 2] = v4.z; lmap[w + 3] = v4.w;
+                }
+                float acc[NA];
 #pragma unroll
-            for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
+                for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
+                constexpr int s0 = 0;
+                if (lv) {  // else every subtree is dead (warp-uniform)
+                    float4 v[GS][Q];
 #pragma unroll
-            for (int s0 = 0; s0 < S::NS; s0 += GS) {
-                const uint64_t gmask = (GS >= 64) ? ~0ull : (((1ull << GS) - 1ull) << s0);
-                if (!(lv & gmask)) continue;  // every subtree of the group is dead (warp-uniform)
-                float4 v[GS][Q];
+                    for (int j = 0; j < GS; ++j) {
+                        const uint32_t lj = (uint32_t)(lv >> (s0 + j)) & 1u;
+                        const uint32_t rot = (lmap[(s0 + j) >> 2] >> (8 * ((s0 + j) & 3))) & 0xFFu;
+                        const float4 *src = tf + ((size_t)(s0 + j) * S::E + line_pos(ent[s0 + j], rot, D)) * Q;
 #pragma unroll
-                for (int j = 0; j < GS; ++j) {
-                    const uint32_t lj = (uint32_t)(lv >> (s0 + j)) & 1u;
-                    const uint32_t rot = (lmap[(s0 + j) >> 2] >> (8 * ((s0 + j) & 3))) & 0xFFu;
-                    const float4 *src = tf + ((size_t)(s0 + j) * S::E + line_pos(ent[s0 + j], rot, D)) * Q;
+                        for (int k = 0; k < Q; ++k) v[j][k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        if (Q == 2) {
+                            ldg_f8_if(src, v[j][0], v[j][Q > 1 ? 1 : 0], lj);
+                        } else {
 #pragma unroll
-                    for (int k = 0; k < Q; ++k) v[j][k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                    if (Q == 2) {
-                        ldg_f8_if(src, v[j][0], v[j][Q > 1 ? 1 : 0], lj);
+                            for (int k = 0; k < Q; ++k) ldg_f4_if(src + k, v[j][k], lj);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < GS; ++j) {
+                        const int r = S::NS - 1 + s0 + j;
+                        const float *vj = reinterpret_cast<const float *>(&v[j][0]);
+#pragma unroll
+                        for (int k = 0; k < D - 2; ++k) acc[((r + 1) >> (D - 2 - k)) - 1] += vj[k];
+                    }
+                    // the three inner nodes of each subtree, in flush order; the next
+                    // batch's phi offsets are read before this batch's phi writes, so the
+                    // offset loads stay off the chain of dependent shared-memory round trips
+                    int o[8];
+                    load_offsets8(fl + 3 * s0, o);
+#pragma unroll
+                    for (int i0 = 0; i0 < 3 * GS; i0 += 8) {
+                        const int fb = 3 * s0 + i0;
+                        int on[8];
+                        if (i0 + 8 < 3 * GS) load_offsets8(fl + fb + 8, on);
+                        float val[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int i = i0 + q;
+                            val[q] = i < 3 * GS ? reinterpret_cast<const float *>(&v[i / 3][0])[D - 2 + i % 3] : 0.0f;
+                        }
+                        if ((real >> (fb >> 3)) & 1u)  // a batch of pass-through nodes only adds nothing
+                            flush_batch(myphi, o, val, min(8, 3 * GS - i0), (fok >> (fb >> 3)) & 1u);
+                        if (i0 + 8 < 3 * GS) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) o[q] = on[q];
+                        }
+                    }
+                }
+                // the nodes above the bottom subtrees
+                if (S::NS > 1) {
+                    int o[8];
+                    load_offsets8(fl + FLB, o);
+#pragma unroll
+                    for (int u0 = 0; u0 < S::NS - 1; u0 += 8) {
+                        int on[8];
+                        if (u0 + 8 < S::NS - 1) load_offsets8(fl + FLB + u0 + 8, on);
+                        float val[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) val[q] = u0 + q < S::NS - 1 ? acc[u0 + q] : 0.0f;
+                        if ((real >> ((FLB + u0) >> 3)) & 1u)
+                            flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u);
+                        if (u0 + 8 < S::NS - 1) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) o[q] = on[q];
+                        }
+                    }
+                }
+            } else {
+                // Deep trees: a loop over the NG gather groups.  Group g holds the subtrees
+                // g*GS .. g*GS + GS - 1, whose roots are the leaves of the group's own
+                // upper subtree (GS - 1 nodes, rooted at level L0); its nodes accumulate
+                // in registers and are flushed with the group, so no accumulator lives
+                // across groups but the NG - 1 nodes above them, each fed one sum per
+                // group (selects that fold away when the loop is unrolled).
+                constexpr int NG = X::NG, GL = flush_group_len(D);
+                constexpr int LG = ilog2(GS), L0 = D - 2 - LG, NU = GS - 1;
+                const uint64_t fok = mt.flush, real = mt.real;
+                // decision bits per level, from the groups' roots down (word 0 also holds
+                // the levels above them)
+                LevelBits<D, L0> lb0(dw);
+                LevelBits<D, L0 + 1 < D ? L0 + 1 : D - 1> lb1(dw);
+                LevelBits<D, L0 + 2 < D ? L0 + 2 : D - 1> lb2(dw);
+                LevelBits<D, L0 + 3 < D ? L0 + 3 : D - 1> lb3(dw);
+                LevelBits<D, D - 2> lbr(dw);
+                LevelBits<D, D - 1> lbc(dw);
+                static_assert(LG <= 4 && L0 <= 3, "group subtrees of at most 4 levels below at most 3 top levels");
+                float top[NG - 1];
+#pragma unroll
+                for (int u = 0; u < NG - 1; ++u) top[u] = 0.0f;
+                const unsigned char *lines = reinterpret_cast<const unsigned char *>(job.lines + (size_t)t * LW);
+#pragma unroll X::GUNROLL
+                for (int g = 0; g < NG; ++g) {
+                    if (!((lv >> (g * GS)) & ((1ull << GS) - 1ull))) continue;  // all dead (warp-uniform)
+                    // the group's line maps, one byte per subtree
+                    uint32_t lm[GS / 4];
+                    if constexpr (GS == 16) {
+                        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(lines) + g);
+                        lm[0] = q.x; lm[1] = q.y; lm[2] = q.z; lm[3] = q.w;
                     } else {
-#pragma unroll
-                        for (int k = 0; k < Q; ++k) ldg_f4_if(src + k, v[j][k], lj);
+                        static_assert(GS == 8, "groups of 8 or 16 subtrees");
+                        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(lines) + g);
+                        lm[0] = q.x; lm[1] = q.y;
                     }
-                }
+                    // path bits from the root to the group's root (exclusive), then the
+                    // raw decisions of the group's upper nodes, as in subtree_entries
+                    uint32_t P = 0u;
 #pragma unroll
-                for (int j = 0; j < GS; ++j) {
-                    const int r = S::NS - 1 + s0 + j;
-                    const float *vj = reinterpret_cast<const float *>(&v[j][0]);
+                    for (int k = 0; k < L0; ++k) P = (P << 1) | ((dw[0] >> ((1 << k) - 1 + (g >> (L0 - k)))) & 1u);
+                    uint32_t ub = lb0.template field<1>(g);
+                    if constexpr (LG > 1) ub |= lb1.template field<(LG > 1 ? 2 : 1)>(g) << 1;
+                    if constexpr (LG > 2) ub |= lb2.template field<(LG > 2 ? 4 : 1)>(g) << 3;
+                    if constexpr (LG > 3) ub |= lb3.template field<(LG > 3 ? 8 : 1)>(g) << 7;
+                    const uint32_t rb = lbr.template field<GS>(g);
+                    const uint32_t cb = lbc.template field<2 * GS>(g);
+                    uint32_t R[NU];
 #pragma unroll
-                    for (int k = 0; k < D - 2; ++k) acc[((r + 1) >> (D - 2 - k)) - 1] += vj[k];
-                }
-                // the three inner nodes of each subtree of the group, in flush order; the
-                // next batch's phi offsets are read before this batch's phi writes, so the
-                // offset loads stay off the chain of dependent shared-memory round trips
-                int o[8];
-                load_offsets8(fl + 3 * s0, o);
+                    for (int u = 0; u < NU; ++u) R[u] = ((u == 0 ? P : R[(u - 1) >> 1]) << 1) | ((ub >> u) & 1u);
+                    float4 v[GS][Q];
 #pragma unroll
-                for (int i0 = 0; i0 < 3 * GS; i0 += 8) {
-                    const int fb = 3 * s0 + i0;
-                    int on[8];
-                    if (i0 + 8 < 3 * GS) load_offsets8(fl + fb + 8, on);
-                    float val[8];
+                    for (int j = 0; j < GS; ++j) {
+                        const int s = g * GS + j;
+                        const uint32_t ent = (R[(GS - 2 + j) >> 1] << 3) | (((rb >> j) & 1u) << 2) | ((cb >> (2 * j)) & 3u);
+                        const uint32_t lj = (uint32_t)(lv >> s) & 1u;
+                        const uint32_t rot = (lm[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+                        const float4 *src = tf + ((size_t)s * S::E + line_pos(ent, rot, D)) * Q;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int i = i0 + q;
-                        val[q] = i < 3 * GS ? reinterpret_cast<const float *>(&v[i / 3][0])[D - 2 + i % 3] : 0.0f;
+                        for (int k = 0; k < Q; ++k) v[j][k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        if (Q == 2) {
+                            ldg_f8_if(src, v[j][0], v[j][Q > 1 ? 1 : 0], lj);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < Q; ++k) ldg_f4_if(src + k, v[j][k], lj);
+                        }
                     }
-                    if ((real >> (fb >> 3)) & 1u)  // a batch of pass-through nodes only adds nothing
-                        flush_batch(myphi, o, val, min(8, 3 * GS - i0), (fok >> (fb >> 3)) & 1u);
-                    if (i0 + 8 < 3 * GS) {
+                    // the group's upper nodes (local heap order) and the per-group sums of
+                    // the levels above it
+                    float gl[NU], xk[L0];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) o[q] = on[q];
+                    for (int u = 0; u < NU; ++u) gl[u] = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < GS; ++j) {
+#pragma unroll
+                        for (int k = 0; k < L0; ++k) xk[k] = j == 0 ? slot_of(v[j], k) : xk[k] + slot_of(v[j], k);
+#pragma unroll
+                        for (int l = 0; l < LG; ++l) gl[(1 << l) - 1 + (j >> (LG - l))] += slot_of(v[j], L0 + l);
                     }
-                }
-            }
-            // the nodes above the bottom subtrees
-            if (S::NS > 1) {
-                int o[8];
-                load_offsets8(fl + FLB, o);
 #pragma unroll
-                for (int u0 = 0; u0 < S::NS - 1; u0 += 8) {
-                    int on[8];
-                    if (u0 + 8 < S::NS - 1) load_offsets8(fl + FLB + u0 + 8, on);
-                    float val[8];
+                    for (int k = 0; k < L0; ++k) {
+                        const int at = g >> (L0 - k);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) val[q] = u0 + q < S::NS - 1 ? acc[u0 + q] : 0.0f;
-                    if ((real >> ((FLB + u0) >> 3)) & 1u)
-                        flush_batch(myphi, o, val, min(8, S::NS - 1 - u0), (fok >> ((FLB + u0) >> 3)) & 1u);
-                    if (u0 + 8 < S::NS - 1) {
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) o[q] = on[q];
+                        for (int p = 0; p < (1 << k); ++p) top[(1 << k) - 1 + p] += p == at ? xk[k] : 0.0f;
                     }
+                    const Off *gfl = fl + g * GL;
+                    flush_run<3 * GS>(myphi, gfl, [&](int i) { return slot_of(v[i / 3], D - 2 + i % 3); }, real, fok,
+                                      g * (GL / 8));
+                    flush_run<NU>(myphi, gfl + FLB, [&](int i) { return gl[i]; }, real, fok, g * (GL / 8) + FLB / 8);
                 }
+                flush_run<NG - 1>(myphi, fl + NG * GL, [&](int i) { return top[i]; }, real, fok, NG * GL / 8);
             }
         }
     }

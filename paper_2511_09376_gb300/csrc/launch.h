@@ -27,6 +27,7 @@ struct ExplainJob {
     TreeArrays ta;
     const float *sfold;     // folded slot vectors [T][NS][2^(D+1)][SP], entry e at line_pos(e)
     const uint32_t *lines;  // per tree lines_words(D) words: byte s = line map of subtree s
+    const int32_t *flfeat;  // [T][flush_len(D)] feature of the node at each flush position (F: none)
     int T, F;
 };
 

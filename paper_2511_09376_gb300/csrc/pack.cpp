@@ -110,6 +110,8 @@ void build_records(Packed *pp) {
     const int64_t blk = 32 * (int64_t)p.code_bytes;             // bytes of one column in a code block
     p.rec.assign((size_t)T * NI, NodeRec{0, -1, 0u, 0u});
     p.meta.assign((size_t)T, TreeMeta{});
+    const int FL = flush_len(D);
+    p.flush_feat.assign((size_t)T * FL, F);
     for (int t = 0; t < T; ++t) {
         TreeMeta &m = p.meta[(size_t)t];
         int c = 0;
@@ -133,6 +135,10 @@ void build_records(Packed *pp) {
         }
         for (int w = (NI - 1) / 32 + 1; w < 8; ++w) m.wend[w] = (uint8_t)c;
         m.live = p.live[(size_t)t];
+        for (int i = 0; i < FL; ++i) {
+            const int v = flush_node(D, i);
+            if (v >= 0) p.flush_feat[(size_t)t * FL + i] = p.node_feat[(size_t)t * NI + v];
+        }
         // flush batches of the consumer kernel whose real features are all distinct
         for (int b = 0; b < flush_batches(D); ++b) {
             bool ok = true;
@@ -143,10 +149,10 @@ void build_records(Packed *pp) {
                     const int32_t fi = p.node_feat[(size_t)t * NI + vi], fj = p.node_feat[(size_t)t * NI + vj];
                     ok = fi == F || fi != fj;  // pass-through nodes all write the scratch row
                 }
-            if (ok) m.flush |= 1u << b;
+            if (ok) m.flush |= 1ull << b;
             for (int i = 8 * b; i < 8 * b + 8; ++i) {
                 const int v = flush_node(D, i);
-                if (v >= 0 && p.node_feat[(size_t)t * NI + v] != F) m.real |= 1u << b;
+                if (v >= 0 && p.node_feat[(size_t)t * NI + v] != F) m.real |= 1ull << b;
             }
         }
     }

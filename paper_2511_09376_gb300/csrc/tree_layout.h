@@ -11,11 +11,15 @@
 // threshold never sends a row left (rank -1).  The kernels stage codes instead of
 // floats: one or two bytes per column and row instead of four per feature.
 //
-// Flush sequence of a tree of depth D (NS = 2^(D-2) bottom subtrees): the three inner
-// nodes r, 2r+1, 2r+2 of every bottom subtree (r = NS - 1 + s, s = 0..NS-1), padded to a
-// multiple of 8; then the inner nodes above the bottom subtrees (0..NS-2), padded to a
-// multiple of 8.  Batch b is positions [8b, 8b + 8).  A batch whose real features are
-// all distinct can read all its phi values before writing any.
+// Flush sequence of a tree of depth D (NS = 2^(D-2) bottom subtrees, cut into NG groups
+// of GS = gather_group(D) consecutive subtrees, the gather groups of the consumer
+// kernel).  Per group g: the three inner nodes r, 2r+1, 2r+2 of each of its subtrees (r =
+// NS - 1 + s), padded to a multiple of 8; then the GS - 1 inner nodes of the height-
+// log2(GS) subtree whose leaves are the group's subtree roots (heap order within it),
+// padded to a multiple of 8.  After the groups: the NG - 1 nodes above them (heap 0 ..
+// NG - 2), padded to a multiple of 8.  With one group (D <= 6) this is all bottom nodes,
+// then all nodes above them.  Batch b is positions [8b, 8b + 8).  A batch whose real
+// features are all distinct can read all its phi values before writing any.
 #pragma once
 #include <cstdint>
 
@@ -41,12 +45,12 @@ struct NodeRec {
 struct TreeMeta {
     uint32_t pt[8];   // bit v of word v/32: inner node v is a pass-through node (always left)
     uint64_t live;    // bit s: bottom subtree s has a non-zero leaf
-    uint32_t flush;   // bit b: consumer flush batch b repeats no real feature
+    uint64_t flush;   // bit b: consumer flush batch b repeats no real feature
     uint8_t wend[8];  // NodeRec index one past the last node of word w
-    uint32_t real;    // bit b: consumer flush batch b holds a real (not pass-through) node
+    uint64_t real;    // bit b: consumer flush batch b holds a real (not pass-through) node
 };
 static_assert(sizeof(NodeRec) == 16, "NodeRec is one 16-byte load");
-static_assert(sizeof(TreeMeta) == 56, "TreeMeta layout");
+static_assert(sizeof(TreeMeta) == 64, "TreeMeta layout");
 
 // One code column: source feature, first threshold in the sorted threshold array,
 // threshold count, and the largest power of two <= count (0 when count is 0).  With
@@ -55,23 +59,43 @@ struct CodeCol {
     int32_t feature, first, count, top;
 };
 
-WDF_HD constexpr int flush_len_bottom(int D) { return (3 * (1 << (D - 2)) + 7) & ~7; }
-WDF_HD constexpr int flush_len_upper(int D) { return ((1 << (D - 2)) - 1 + 7) & ~7; }
-WDF_HD constexpr int flush_len(int D) { return flush_len_bottom(D) + flush_len_upper(D); }
+// Floats per entry of the folded slot vectors: D - 2 ancestors and the three nodes of the
+// bottom subtree, padded to 4, 8 or 12.
+WDF_HD constexpr int slots_per_entry(int D) { return (D + 1) <= 4 ? 4 : ((D + 1) <= 8 ? 8 : 12); }
+// Bottom subtrees per gather group: the largest power of two <= NS whose slot vectors fit
+// in 128 registers.
+WDF_HD constexpr int gather_group(int D) {
+    int g = 1 << (D - 2);
+    while (g > 1 && g * slots_per_entry(D) > 128) g /= 2;
+    return g;
+}
+WDF_HD constexpr int pad8(int n) { return (n + 7) & ~7; }
+WDF_HD constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+WDF_HD constexpr int flush_groups(int D) { return (1 << (D - 2)) / gather_group(D); }
+WDF_HD constexpr int flush_group_bottom(int D) { return pad8(3 * gather_group(D)); }
+WDF_HD constexpr int flush_group_len(int D) { return flush_group_bottom(D) + pad8(gather_group(D) - 1); }
+WDF_HD constexpr int flush_len(int D) { return flush_groups(D) * flush_group_len(D) + pad8(flush_groups(D) - 1); }
 WDF_HD constexpr int flush_batches(int D) { return flush_len(D) / 8; }
 
 // Heap index of the node at flush position i, -1 for padding.
 WDF_HD inline int flush_node(int D, int i) {
-    const int NS = 1 << (D - 2);
-    if (i < 3 * NS) {
-        const int r = NS - 1 + i / 3, c = i % 3;
+    const int NS = 1 << (D - 2), GS = gather_group(D), NG = NS / GS, GL = flush_group_len(D);
+    if (i >= NG * GL) {
+        const int u = i - NG * GL;
+        return u < NG - 1 ? u : -1;
+    }
+    const int g = i / GL, k = i - g * GL;
+    if (k < 3 * GS) {
+        const int r = NS - 1 + g * GS + k / 3, c = k % 3;
         return c == 0 ? r : 2 * r + c;
     }
-    if (i < flush_len_bottom(D)) return -1;
-    const int u = i - flush_len_bottom(D);
-    return u < NS - 1 ? u : -1;
+    const int u = k - flush_group_bottom(D);  // node of the group's upper subtree, heap order
+    if (u < 0 || u >= GS - 1) return -1;
+    const int l = ilog2(u + 1);          // level of u within the group's subtree
+    const int lg = D - 2 - ilog2(GS) + l;  // its level in the tree
+    return (1 << lg) - 1 + g * (1 << l) + (u - ((1 << l) - 1));
 }
 
-static_assert(flush_batches(8) <= 32, "batch flags are one 32-bit word per tree");
+static_assert(flush_batches(8) <= 64, "batch flags are one 64-bit word per tree");
 
 }  // namespace wdf

@@ -28,7 +28,7 @@ struct Shape {
     static constexpr int NS = 1 << (D - 2);    // bottom subtrees
     static constexpr int E = 1 << (D + 1);     // entries per bottom subtree
     static constexpr int NW = (NI + 31) / 32;  // 32-bit decision words
-    static constexpr int SP = (D + 1) <= 4 ? 4 : ((D + 1) <= 8 ? 8 : 12);  // padded slots per entry
+    static constexpr int SP = slots_per_entry(D);  // padded slots per entry
 };
 
 // Stage the node records and metadata of trees [t0, t0 + tcn) into shared memory (all

@@ -42,6 +42,8 @@ struct Packed {
     // columns and their sorted thresholds
     std::vector<NodeRec> rec;         // [T][NI]
     std::vector<TreeMeta> meta;       // [T]
+    std::vector<int32_t> flush_feat;  // [T][flush_len(D)] feature at each consumer flush position (F: padding
+                                      // and pass-through nodes)
     std::vector<CodeCol> cols;        // [n_cols]
     std::vector<float> col_thr;       // column segments of the sorted distinct thresholds
     int code_bytes = 1;               // 1 or 2
