@@ -34,7 +34,7 @@ struct ExplainCfg {
     // trees per shared-memory chunk: two keeps the block small (five blocks of 64 rows
     // per SM at 127 features), measured faster than eight despite four times the barriers;
     // one at depth 8, whose node records would otherwise cost a block per SM (four
-    // instead of three 64-row blocks at 134 features: 25 % faster)
+    // instead of three 64-row blocks at 134 features)
     static constexpr int TCH = D >= 8 ? 1 : 2;
     // bottom subtrees gathered together (tree_layout.h); deep trees have several groups
     static constexpr int GS = gather_group(D);
@@ -221,25 +221,59 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
     for (int i = tid; i < (F + 1) * XS; i += TC) sp[i] = 0.0f;
     float *myphi = sp + tid;
     const CodeReader xr(sx + (size_t)warp * 32 * xb, lane, cb);
+    // The next chunk's node records, metadata and flush features are loaded into
+    // registers while this chunk's trees are processed, so staging a chunk costs only
+    // shared-memory stores between two barriers (a block alone on its SM -- a small
+    // request -- would otherwise wait for a global round trip per chunk).
+    constexpr int MW = (int)(sizeof(TreeMeta) / sizeof(uint2));
+    constexpr int RPT = (X::TCH * S::NI + TC - 1) / TC, MPT = (X::TCH * MW + TC - 1) / TC;
+    constexpr int FPT = (X::TCH * FL + TC - 1) / TC;
+    int4 prec[RPT];
+    uint2 pmeta[MPT];
+    int pfl[FPT];
+    auto fetch = [&](int t0) {
+        const int n = min(X::TCH, T - t0);
+        const int4 *rsrc = reinterpret_cast<const int4 *>(ta.rec) + (size_t)t0 * S::NI;
+        const uint2 *msrc = reinterpret_cast<const uint2 *>(ta.meta + t0);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int i = tid + r * TC;
+            if (i < n * S::NI) prec[r] = __ldg(rsrc + i);
+        }
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            const int i = tid + m * TC;
+            if (i < n * MW) pmeta[m] = __ldg(msrc + i);
+        }
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int i = tid + f * TC;
+            if (i < n * FL) pfl[f] = __ldg(job.flfeat + (size_t)t0 * FL + i);
+        }
+    };
+    fetch(0);
     for (int tc0 = 0; tc0 < T; tc0 += X::TCH) {
         const int tcn = min(X::TCH, T - tc0);
         __syncthreads();
-        stage_trees<D>(tc0, tcn, ta.rec, ta.meta, srec, smeta, tid, TC);
         // phi offsets of every tree in flush order (padding and pass-through nodes: the
-        // scratch row F), from the features the host lists in flush order.  Depth 8
-        // recomputes the positions here instead: measured 13 % faster at 1000 trees (the
-        // longer staging step changes how the blocks share the instruction cache and L2:
-        // 0.36e9 instead of 0.66e9 instruction-cache misses, L2 hit rate 96 % instead of
-        // 85 %), while depths 6 and 7 are 3-10 % faster with the list.
-        if constexpr (D >= 8) {
-            for (int i = tid; i < tcn * FL; i += TC) {
-                const int g = i / FL, v = flush_node(D, i - g * FL);
-                sfl[i] = (Off)((v >= 0 ? __ldg(&ta.nodes[(size_t)(tc0 + g) * S::NI + v].x) : F) * XS);
-            }
-        } else {
-            for (int i = tid; i < tcn * FL; i += TC) sfl[i] = (Off)(__ldg(job.flfeat + (size_t)tc0 * FL + i) * XS);
+        // scratch row F), from the features the host lists in flush order
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int i = tid + r * TC;
+            if (i < tcn * S::NI) srec[i] = prec[r];
+        }
+#pragma unroll
+        for (int m = 0; m < MPT; ++m) {
+            const int i = tid + m * TC;
+            if (i < tcn * MW) reinterpret_cast<uint2 *>(smeta)[i] = pmeta[m];
+        }
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) {
+            const int i = tid + f * TC;
+            if (i < tcn * FL) sfl[i] = (Off)(pfl[f] * XS);
         }
         __syncthreads();
+        if (tc0 + X::TCH < T) fetch(tc0 + X::TCH);
         for (int g = 0; g < tcn; ++g) {
             const int t = tc0 + g;
             const TreeMeta &mt = smeta[g];
