@@ -81,6 +81,13 @@ struct BgLayout {
     }
 };
 
+// 16-byte code words per thread of the next tile held in registers (512-row tiles of up to
+// 128 one-byte codes per row fit entirely): 1.8 % off the large workload's background
+// step.  None at depth 5, where the registers made the compiler spill, nor for deep
+// trees, whose decision loop needs them.
+template <int D>
+__host__ __device__ constexpr int bg_prefetch() { return D <= 6 && D != 5 ? 8 : 0; }
+
 // codes: rows [0, m) of one encoded chunk, padded to a multiple of RT rows.
 template <int D, int RT, bool SMEM>
 __global__ void __launch_bounds__(RT) k_bg_hist(const unsigned char *__restrict__ codes, int64_t m, TreeArrays ta,
@@ -105,17 +112,37 @@ __global__ void __launch_bounds__(RT) k_bg_hist(const unsigned char *__restrict_
         for (int i = tid; i < bins / 2; i += RT) sh[i] = 0u;
     const CodeReader xr(sx + (size_t)warp * 32 * xb, lane, cb);
     const int tile16 = RT * xb / 16;
+    // The first bg_prefetch 16-byte words per thread of the next tile are loaded into
+    // registers while the current tile is counted (the rest, for wide rows, at staging).
+    constexpr int PF = bg_prefetch<D>();
+    uint4 pf[PF > 0 ? PF : 1];
+    auto fetch = [&](int64_t r0) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(codes + r0 * xb);
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const int i = tid + k * RT;
+            if (i < tile16) pf[k] = __ldg(src + i);
+        }
+    };
+    const int64_t step = (int64_t)nslices * RT;
+    if (PF > 0 && (int64_t)slice * RT < m) fetch((int64_t)slice * RT);
     int64_t since_flush = 0;
-    for (int64_t row0 = (int64_t)slice * RT; row0 < m; row0 += (int64_t)nslices * RT) {
+    for (int64_t row0 = (int64_t)slice * RT; row0 < m; row0 += step) {
         __syncthreads();
         if (SMEM && since_flush + RT > 65535) {  // a 16-bit counter could overflow: flush
             bg_flush<D>(sh, gdst, bins, tid, RT);
             since_flush = 0;
         }
         // the tile's RT rows are RT / 32 consecutive code blocks
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const int i = tid + k * RT;
+            if (i < tile16) reinterpret_cast<uint4 *>(sx)[i] = pf[k];
+        }
         const uint4 *src = reinterpret_cast<const uint4 *>(codes + row0 * xb);
-        for (int i = tid; i < tile16; i += RT) reinterpret_cast<uint4 *>(sx)[i] = __ldg(src + i);
+        for (int i = tid + PF * RT; i < tile16; i += RT) reinterpret_cast<uint4 *>(sx)[i] = __ldg(src + i);
         __syncthreads();
+        if (PF > 0 && row0 + step < m) fetch(row0 + step);
         since_flush += RT;
         const bool valid = row0 + tid < m;
         for (int g = 0; g < g_cnt; ++g) {
