@@ -32,10 +32,11 @@ namespace wdf {
 template <int D>
 struct ExplainCfg {
     // trees per shared-memory chunk: two keeps the block small (five blocks of 64 rows
-    // per SM at 127 features), measured faster than eight despite four times the barriers;
-    // one at depth 8, whose node records would otherwise cost a block per SM (four
-    // instead of three 64-row blocks at 134 features)
-    static constexpr int TCH = D >= 8 ? 1 : 2;
+    // per SM at 127 features), measured faster than eight despite four times the barriers
+    // (and than one or three, within 1 %); one for deep trees, whose node records would
+    // otherwise cost a block per SM (depth 8: four instead of three 64-row blocks at 134
+    // features; depth 7: 2 % faster)
+    static constexpr int TCH = D >= 7 ? 1 : 2;
     // bottom subtrees gathered together (tree_layout.h); deep trees have several groups
     static constexpr int GS = gather_group(D);
     static constexpr int NG = Shape<D>::NS / GS;
