@@ -86,7 +86,7 @@ namespace {
 void free_ensemble(wdf_ensemble *e) {
     dfree(e->d_nodes); dfree(e->d_keys); dfree(e->d_group_leaf); dfree(e->d_leaf_row);
     dfree(e->d_w_rows); dfree(e->d_tiles); dfree(e->d_t32);
-    dfree(e->d_rec); dfree(e->d_meta); dfree(e->d_flfeat); dfree(e->d_cols); dfree(e->d_col_thr);
+    dfree(e->d_rec); dfree(e->d_meta); dfree(e->d_flfeat); dfree(e->d_xmask); dfree(e->d_cols); dfree(e->d_col_thr);
     dfree(e->d_apk); dfree(e->d_bpk); dfree(e->d_tiles128); dfree(e->d_err); dfree(e->d_A); dfree(e->d_ratio);
     dfree(e->d_hist); dfree(e->d_vc); dfree(e->d_scale); dfree(e->d_S); dfree(e->d_sfold); dfree(e->d_base);
     dfree(e->d_lines);
@@ -366,6 +366,7 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
     chk(dalloc(&e->d_rec, p.rec.size(), &e->bytes));
     chk(dalloc(&e->d_meta, p.meta.size(), &e->bytes));
     chk(dalloc(&e->d_flfeat, p.flush_feat.size(), &e->bytes));
+    if (!p.xmask.empty()) chk(dalloc(&e->d_xmask, p.xmask.size(), &e->bytes));
     chk(dalloc(&e->d_cols, p.cols.size(), &e->bytes));
     chk(dalloc(&e->d_col_thr, std::max<size_t>(p.col_thr.size(), 1), &e->bytes));
     if (ce == cudaSuccess) {
@@ -379,6 +380,8 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
         chk(cudaMemcpy(e->d_rec, p.rec.data(), p.rec.size() * sizeof(wdf::NodeRec), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(e->d_meta, p.meta.data(), p.meta.size() * sizeof(wdf::TreeMeta), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(e->d_flfeat, p.flush_feat.data(), p.flush_feat.size() * 4, cudaMemcpyHostToDevice));
+        if (!p.xmask.empty())
+            chk(cudaMemcpy(e->d_xmask, p.xmask.data(), p.xmask.size() * 8, cudaMemcpyHostToDevice));
         chk(cudaMemcpy(e->d_cols, p.cols.data(), p.cols.size() * sizeof(wdf::CodeCol), cudaMemcpyHostToDevice));
         if (!p.col_thr.empty())
             chk(cudaMemcpy(e->d_col_thr, p.col_thr.data(), p.col_thr.size() * 4, cudaMemcpyHostToDevice));

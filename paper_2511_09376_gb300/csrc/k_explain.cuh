@@ -48,22 +48,29 @@ struct ExplainCfg {
     // phi offsets of the flush positions: 16 bits for deep trees (every offset is below
     // the 58,112 floats a block's shared memory can hold), 32 bits otherwise
     using Off = typename std::conditional<(D >= 7), uint16_t, int>::type;
+    // node records staged as their first eight bytes (column offset, rank) with the
+    // tree's expand masks, decisions collected in record order (tree_decisions8): up to
+    // depth 6, where a tree's decisions fit one 64-bit word
+    static constexpr bool R8 = D <= 6;
+    using Rec = typename std::conditional<R8, int2, int4>::type;
 };
 
 // Shared memory of one block: code tile (TC rows x xb bytes) | phi tile ((F + 1) x (TC + 1)
-// floats, feature-major, row F a scratch row) | tree metadata | node records | phi
-// offsets of the trees' nodes in flush order.
+// floats, feature-major, row F a scratch row) | tree metadata | expand masks (depth <= 6)
+// | node records | phi offsets of the trees' nodes in flush order.
 template <int D>
 struct ExLayout {
-    size_t x, p, meta, rec, fl, total;
+    size_t x, p, meta, xm, rec, fl, total;
     static __host__ __device__ size_t up(size_t v) { return (v + 15) & ~(size_t)15; }
     __host__ __device__ ExLayout(int F, int xb, int TC) {
+        using X = ExplainCfg<D>;
         x = up((size_t)TC * xb);
         p = up((size_t)(F + 1) * (TC + 1) * 4);
-        meta = up((size_t)ExplainCfg<D>::TCH * sizeof(TreeMeta));
-        rec = up((size_t)ExplainCfg<D>::TCH * Shape<D>::NI * sizeof(NodeRec));
-        fl = up((size_t)ExplainCfg<D>::TCH * flush_len(D) * sizeof(typename ExplainCfg<D>::Off));
-        total = x + p + meta + rec + fl;
+        meta = up((size_t)X::TCH * sizeof(TreeMeta));
+        xm = X::R8 ? up((size_t)X::TCH * 6 * 8) : 0;
+        rec = up((size_t)X::TCH * Shape<D>::NI * sizeof(typename X::Rec));
+        fl = up((size_t)X::TCH * flush_len(D) * sizeof(typename X::Off));
+        total = x + p + meta + xm + rec + fl;
     }
 };
 
@@ -212,8 +219,10 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
     unsigned char *sx = smem_raw;
     float *sp = reinterpret_cast<float *>(smem_raw + L.x);
     TreeMeta *smeta = reinterpret_cast<TreeMeta *>(smem_raw + L.x + L.p);
-    int4 *srec = reinterpret_cast<int4 *>(smem_raw + L.x + L.p + L.meta);
-    Off *sfl = reinterpret_cast<Off *>(smem_raw + L.x + L.p + L.meta + L.rec);
+    using Rec = typename X::Rec;
+    unsigned long long *sxm = reinterpret_cast<unsigned long long *>(smem_raw + L.x + L.p + L.meta);
+    Rec *srec = reinterpret_cast<Rec *>(smem_raw + L.x + L.p + L.meta + L.xm);
+    Off *sfl = reinterpret_cast<Off *>(smem_raw + L.x + L.p + L.meta + L.xm + L.rec);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(codes + c0 * xb);
@@ -228,18 +237,25 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
     // request -- would otherwise wait for a global round trip per chunk).
     constexpr int MW = (int)(sizeof(TreeMeta) / sizeof(uint2));
     constexpr int RPT = (X::TCH * S::NI + TC - 1) / TC, MPT = (X::TCH * MW + TC - 1) / TC;
-    constexpr int FPT = (X::TCH * FL + TC - 1) / TC;
-    int4 prec[RPT];
+    constexpr int FPT = (X::TCH * FL + TC - 1) / TC, XPT = X::R8 ? (X::TCH * 6 + TC - 1) / TC : 0;
+    Rec prec[RPT];
     uint2 pmeta[MPT];
     int pfl[FPT];
+    unsigned long long pxm[XPT > 0 ? XPT : 1];
     auto fetch = [&](int t0) {
         const int n = min(X::TCH, T - t0);
-        const int4 *rsrc = reinterpret_cast<const int4 *>(ta.rec) + (size_t)t0 * S::NI;
+        // a record's first eight bytes are its column offset and rank (NodeRec)
+        const Rec *rsrc = reinterpret_cast<const Rec *>(ta.rec) + (size_t)t0 * S::NI * (X::R8 ? 2 : 1);
         const uint2 *msrc = reinterpret_cast<const uint2 *>(ta.meta + t0);
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             const int i = tid + r * TC;
-            if (i < n * S::NI) prec[r] = __ldg(rsrc + i);
+            if (i < n * S::NI) prec[r] = __ldg(rsrc + (X::R8 ? 2 * i : i));
+        }
+#pragma unroll
+        for (int k = 0; k < XPT; ++k) {
+            const int i = tid + k * TC;
+            if (i < n * 6) pxm[k] = __ldg(job.xmask + (size_t)t0 * 6 + i);
         }
 #pragma unroll
         for (int m = 0; m < MPT; ++m) {
@@ -269,6 +285,11 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
             if (i < tcn * MW) reinterpret_cast<uint2 *>(smeta)[i] = pmeta[m];
         }
 #pragma unroll
+        for (int k = 0; k < XPT; ++k) {
+            const int i = tid + k * TC;
+            if (i < tcn * 6) sxm[i] = pxm[k];
+        }
+#pragma unroll
         for (int f = 0; f < FPT; ++f) {
             const int i = tid + f * TC;
             if (i < tcn * FL) sfl[i] = (Off)(pfl[f] * XS);
@@ -284,7 +305,11 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
             // this loop measured slower here, unlike in the counting kernel; node words
             // packed four to a 16-byte load measured slower too: the decoding cost more
             // issue slots than the shared-memory wavefronts it saved)
-            tree_decisions<D, false>(srec + g * S::NI, mt, xr, dw);
+            if constexpr (X::R8)
+                tree_decisions8<D, false>(srec + g * S::NI, mt.wend[S::NW - 1], mt.pt,
+                                          reinterpret_cast<const uint64_t *>(sxm + g * 6), xr, dw);
+            else
+                tree_decisions<D, false>(srec + g * S::NI, mt, xr, dw);
             const uint64_t lv = mt.live;
             const float4 *tf = reinterpret_cast<const float4 *>(sfold + (size_t)t * S::NS * S::E * S::SP);
             constexpr int LW = lines_words(D);

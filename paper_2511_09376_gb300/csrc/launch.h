@@ -28,6 +28,7 @@ struct ExplainJob {
     const float *sfold;     // folded slot vectors [T][NS][2^(D+1)][SP], entry e at line_pos(e)
     const uint32_t *lines;  // per tree lines_words(D) words: byte s = line map of subtree s
     const int32_t *flfeat;  // [T][flush_len(D)] feature of the node at each flush position (F: none)
+    const unsigned long long *xmask;  // [T][6] (depth <= 6) expand masks of the real nodes
     int T, F;
 };
 

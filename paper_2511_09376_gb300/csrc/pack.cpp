@@ -112,6 +112,7 @@ void build_records(Packed *pp) {
     p.meta.assign((size_t)T, TreeMeta{});
     const int FL = flush_len(D);
     p.flush_feat.assign((size_t)T * FL, F);
+    if (D <= 6) p.xmask.assign((size_t)T * 6, 0ull);
     for (int t = 0; t < T; ++t) {
         TreeMeta &m = p.meta[(size_t)t];
         int c = 0;
@@ -135,6 +136,11 @@ void build_records(Packed *pp) {
         }
         for (int w = (NI - 1) / 32 + 1; w < 8; ++w) m.wend[w] = (uint8_t)c;
         m.live = p.live[(size_t)t];
+        if (D <= 6) {  // the real (not pass-through) nodes, one bit per heap position
+            const uint64_t all = NI == 64 ? ~0ull : ((1ull << NI) - 1ull);
+            const uint64_t real = ~((uint64_t)m.pt[0] | ((uint64_t)m.pt[1] << 32)) & all;
+            expand_masks(real, &p.xmask[(size_t)t * 6]);
+        }
         for (int i = 0; i < FL; ++i) {
             const int v = flush_node(D, i);
             if (v >= 0) p.flush_feat[(size_t)t * FL + i] = p.node_feat[(size_t)t * NI + v];

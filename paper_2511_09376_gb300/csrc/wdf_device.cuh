@@ -87,6 +87,39 @@ __device__ __forceinline__ TreeMeta load_meta(const TreeMeta *p) {
     return m;
 }
 
+// Decision words of one row for one tree of depth <= 6 from the first eight bytes of its
+// node records (code-column offset, rank), rec and the tree's expand masks mv in shared
+// memory: the decisions are collected in record order, one bit per real node, then moved
+// to the nodes' heap positions by the expand of Hacker's Delight section 7-5 (six masked
+// shifts); pass-through nodes add their always-left bits pt.  A 16-byte record read by a
+// whole warp from one shared address takes two L1 wavefronts, an 8-byte one takes one.
+template <int D, bool ONE_BYTE>
+__device__ __forceinline__ void tree_decisions8(const int2 *rec, int cnt, const uint32_t *pt, const uint64_t *mv,
+                                                const CodeReader &xr, uint32_t (&dw)[Shape<D>::NW]) {
+    static_assert(Shape<D>::NW <= 2, "64-bit decision word");
+    uint64_t x = 0ull;
+    int i = 0;
+    for (; i + 4 <= cnt; i += 4) {
+        const int2 a = rec[i], b = rec[i + 1], c = rec[i + 2], d = rec[i + 3];
+        const uint32_t nib = (uint32_t)(xr.code<ONE_BYTE>(a.x) <= a.y) |
+                             ((uint32_t)(xr.code<ONE_BYTE>(b.x) <= b.y) << 1) |
+                             ((uint32_t)(xr.code<ONE_BYTE>(c.x) <= c.y) << 2) |
+                             ((uint32_t)(xr.code<ONE_BYTE>(d.x) <= d.y) << 3);
+        x |= (uint64_t)nib << i;
+    }
+    for (; i < cnt; ++i) {
+        const int2 a = rec[i];
+        x |= (uint64_t)(xr.code<ONE_BYTE>(a.x) <= a.y) << i;
+    }
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {
+        const uint64_t v = mv[k];
+        x = (x & ~v) | ((x << (1 << k)) & v);
+    }
+    dw[0] = pt[0] | (uint32_t)x;
+    if constexpr (Shape<D>::NW == 2) dw[1] = pt[1] | (uint32_t)(x >> 32);
+}
+
 // Decision words of one row for one tree: bit v of word v/32 is 1 when the row goes
 // left at inner node v.  rec (shared memory) holds the tree's real inner nodes.
 template <int D, bool ONE_BYTE>

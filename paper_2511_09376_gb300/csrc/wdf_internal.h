@@ -44,6 +44,7 @@ struct Packed {
     std::vector<TreeMeta> meta;       // [T]
     std::vector<int32_t> flush_feat;  // [T][flush_len(D)] feature at each consumer flush position (F: padding
                                       // and pass-through nodes)
+    std::vector<uint64_t> xmask;      // [T][6] (depth <= 6) expand_masks of the tree's real nodes
     std::vector<CodeCol> cols;        // [n_cols]
     std::vector<float> col_thr;       // column segments of the sorted distinct thresholds
     int code_bytes = 1;               // 1 or 2
@@ -78,6 +79,21 @@ struct TraceRange {
     TraceRange(const TraceRange &) = delete;
     TraceRange &operator=(const TraceRange &) = delete;
 };
+
+// Move masks of the expand of Hacker's Delight section 7-5 for mask m: expanding x with
+// them puts bit k of x at the position of the k-th set bit of m (bits of x at or above
+// popcount(m) must be zero).  Six steps, for shifts of 32, 16, ..., 1.
+inline void expand_masks(uint64_t m, uint64_t mv[6]) {
+    uint64_t mk = ~m << 1;  // bit p: the number of zeros of m below p is odd, after the prefix steps
+    for (int i = 0; i < 6; ++i) {
+        uint64_t mp = mk ^ (mk << 1);
+        for (int s = 2; s < 64; s <<= 1) mp ^= mp << s;
+        const uint64_t v = mp & m;  // the bits of m that move 2^i further in this step
+        mv[i] = v;
+        m = (m ^ v) | (v >> (1 << i));
+        mk &= ~mp;
+    }
+}
 
 inline int slot_pad(int D) { return (D + 1) <= 4 ? 4 : ((D + 1) <= 8 ? 8 : 12); }
 

@@ -31,6 +31,7 @@ struct wdf_ensemble {
     wdf::NodeRec *d_rec = nullptr;
     wdf::TreeMeta *d_meta = nullptr;
     int32_t *d_flfeat = nullptr;  // features in consumer flush order (Packed::flush_feat)
+    unsigned long long *d_xmask = nullptr;  // per tree expand masks of the real nodes (depth <= 6)
     wdf::CodeCol *d_cols = nullptr;
     float *d_col_thr = nullptr;
     // tensor-core contraction: split operand stages (A for any mode, B for bpk_mode),
@@ -44,7 +45,7 @@ struct wdf_ensemble {
     wdf::TreeArrays arrays() const {
         return wdf::TreeArrays{d_nodes, d_rec, d_meta, d_cols, d_col_thr, (int)pk.cols.size(), pk.code_bytes};
     }
-    wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, d_lines, d_flfeat, pk.T, pk.F}; }
+    wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, d_lines, d_flfeat, d_xmask, pk.T, pk.F}; }
     // background state (set_background)
     int has_bg = 0;
     int64_t m = 0;
