@@ -255,7 +255,7 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
 #pragma unroll
         for (int k = 0; k < XPT; ++k) {
             const int i = tid + k * TC;
-            if (i < n * 6) pxm[k] = __ldg(job.xmask + (size_t)t0 * 6 + i);
+            if (i < n * 6) pxm[k] = __ldg(ta.xmask + (size_t)t0 * 6 + i);
         }
 #pragma unroll
         for (int m = 0; m < MPT; ++m) {

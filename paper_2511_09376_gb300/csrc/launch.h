@@ -20,6 +20,7 @@ struct TreeArrays {
     const CodeCol *cols;      // [n_cols] decision-code columns
     const float *col_thr;     // their sorted thresholds
     int n_cols, code_bytes;   // code_bytes: 1 or 2
+    const unsigned long long *xmask;  // [T][6] (depth <= 6) expand masks of the real nodes
 };
 
 // Everything the consumer kernel needs about one ensemble.
@@ -28,7 +29,6 @@ struct ExplainJob {
     const float *sfold;     // folded slot vectors [T][NS][2^(D+1)][SP], entry e at line_pos(e)
     const uint32_t *lines;  // per tree lines_words(D) words: byte s = line map of subtree s
     const int32_t *flfeat;  // [T][flush_len(D)] feature of the node at each flush position (F: none)
-    const unsigned long long *xmask;  // [T][6] (depth <= 6) expand masks of the real nodes
     int T, F;
 };
 

@@ -43,9 +43,10 @@ struct wdf_ensemble {
     int n_tiles128 = 0;
     int *d_err = nullptr;
     wdf::TreeArrays arrays() const {
-        return wdf::TreeArrays{d_nodes, d_rec, d_meta, d_cols, d_col_thr, (int)pk.cols.size(), pk.code_bytes};
+        return wdf::TreeArrays{d_nodes, d_rec, d_meta, d_cols, d_col_thr, (int)pk.cols.size(), pk.code_bytes,
+                              d_xmask};
     }
-    wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, d_lines, d_flfeat, d_xmask, pk.T, pk.F}; }
+    wdf::ExplainJob job() const { return wdf::ExplainJob{arrays(), d_sfold, d_lines, d_flfeat, pk.T, pk.F}; }
     // background state (set_background)
     int has_bg = 0;
     int64_t m = 0;
