@@ -236,7 +236,7 @@ wdf_status ensure_frequency_state(wdf_ensemble *ens, wdf_precision precision) {
         WDF_CUDA(dalloc(&ens->d_A, (size_t)ens->n_live * K, &ens->bytes));
         WDF_CUDA(dalloc(&ens->d_scale, (size_t)ens->n_live, &ens->bytes));
         WDF_CUDA(dalloc(&ens->d_S, (size_t)ens->n_live * N, &ens->bytes));
-        WDF_CUDA(dalloc(&ens->d_sfold, hist_n * wdf::slot_pad(p.D), &ens->bytes));
+        WDF_CUDA(dalloc(&ens->d_sfold, hist_n * wdf::slots_per_entry(p.D), &ens->bytes));
         WDF_CUDA(dalloc(&ens->d_lines, (size_t)p.T * wdf::lines_words(p.D), &ens->bytes));
         WDF_CUDA(dalloc(&ens->d_base, 1, &ens->bytes));
     }

@@ -95,6 +95,5 @@ inline void expand_masks(uint64_t m, uint64_t mv[6]) {
     }
 }
 
-inline int slot_pad(int D) { return (D + 1) <= 4 ? 4 : ((D + 1) <= 8 ? 8 : 12); }
 
 }  // namespace wdf
