@@ -43,7 +43,8 @@ struct ExplainCfg {
     static_assert(Shape<D>::NS % GS == 0, "gather groups must tile the bottom subtrees");
     // the group loop is unrolled: rolled (group index in a register, its decision fields
     // and ancestor slots selected at run time) it had no instruction-cache misses at
-    // depth 8 but 13 % more instructions, and measured slower
+    // depth 8 but more instructions; alone it measured within 2 %, in the server (beside
+    // the other depths' kernels) its p99 was 10 % worse
     static constexpr int GUNROLL = NG;
     // phi offsets of the flush positions: 16 bits for deep trees (every offset is below
     // the 58,112 floats a block's shared memory can hold), 32 bits otherwise
@@ -193,7 +194,7 @@ struct LevelBits {
     }
 };
 
-// One tile of TC consumer rows// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble.  The
+// One tile of TC consumer rows starting at row c0 (of n rows), for one ensemble.  The
 // rows' decision codes are copied from codes, the code blocks of all n rows written by
 // k_encode_codes or k_encode_batch (padded to a multiple of TC rows).  Encoding inside
 // the tile measured 1.9 ms per 1M rows slower at the large workload: ten warps per SM
@@ -272,8 +273,6 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
     for (int tc0 = 0; tc0 < T; tc0 += X::TCH) {
         const int tcn = min(X::TCH, T - tc0);
         __syncthreads();
-        // phi offsets of every tree in flush order (padding and pass-through nodes: the
-        // scratch row F), from the features the host lists in flush order
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             const int i = tid + r * TC;
@@ -289,6 +288,8 @@ __device__ __forceinline__ void explain_tile(const ExplainJob &job, const unsign
             const int i = tid + k * TC;
             if (i < tcn * 6) sxm[i] = pxm[k];
         }
+        // phi offsets of every tree in flush order (padding and pass-through nodes: the
+        // scratch row F), from the features the host lists in flush order
 #pragma unroll
         for (int f = 0; f < FPT; ++f) {
             const int i = tid + f * TC;
