@@ -19,6 +19,10 @@ CASES = {
     "d3-ragged": (32, 200, 6000, 12, 8, 25, 3, 0.5, 0.2, False),
     "d4-complete": (33, 200, 6000, 24, 20, 20, 4, 0.3, 0.0, True),
     "d5-ragged": (34, 200, 6000, 60, 40, 20, 5, 0.2, 0.1, False),
+    # depth 6: every one of the 63 nodes real (decision bits 0-62 in record order), and
+    # many early leaves (real-node counts on both sides of 32)
+    "d6-complete": (37, 200, 6000, 50, 40, 20, 6, 0.2, 0.0, True),
+    "d6-ragged": (38, 200, 6000, 50, 40, 40, 6, 0.2, 0.15, False),
     "d7-ragged": (35, 150, 6000, 40, 30, 15, 7, 0.1, 0.1, False),
     "d8-ragged": (36, 150, 6000, 40, 30, 15, 8, 0.1, 0.1, False),
 }
