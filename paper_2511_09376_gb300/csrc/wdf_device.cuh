@@ -91,8 +91,10 @@ __device__ __forceinline__ TreeMeta load_meta(const TreeMeta *p) {
 // node records (code-column offset, rank), rec and the tree's expand masks mv in shared
 // memory: the decisions are collected in record order, one bit per real node, then moved
 // to the nodes' heap positions by the expand of Hacker's Delight section 7-5 (six masked
-// shifts); pass-through nodes add their always-left bits pt.  A 16-byte record read by a
-// whole warp from one shared address takes two L1 wavefronts, an 8-byte one takes one.
+// shifts); pass-through nodes add their always-left bits pt, which also cover the copies
+// the expand leaves outside the real positions (or past the tree's last node).  A
+// 16-byte record read by a whole warp from one shared address takes two L1 wavefronts,
+// an 8-byte one takes one.
 template <int D, bool ONE_BYTE>
 __device__ __forceinline__ void tree_decisions8(const int2 *rec, int cnt, const uint32_t *pt, const uint64_t *mv,
                                                 const CodeReader &xr, uint32_t (&dw)[Shape<D>::NW]) {

@@ -82,7 +82,9 @@ struct TraceRange {
 
 // Move masks of the expand of Hacker's Delight section 7-5 for mask m: expanding x with
 // them puts bit k of x at the position of the k-th set bit of m (bits of x at or above
-// popcount(m) must be zero).  Six steps, for shifts of 32, 16, ..., 1.
+// popcount(m) must be zero) and leaves copies of bits only at positions outside m, which
+// the consumer kernel ORs with the pass-through bits (all ones there) instead of
+// masking.  Six steps, for shifts of 32, 16, ..., 1.
 inline void expand_masks(uint64_t m, uint64_t mv[6]) {
     uint64_t mk = ~m << 1;  // bit p: the number of zeros of m below p is odd, after the prefix steps
     for (int i = 0; i < 6; ++i) {
@@ -94,6 +96,5 @@ inline void expand_masks(uint64_t m, uint64_t mv[6]) {
         mk &= ~mp;
     }
 }
-
 
 }  // namespace wdf
