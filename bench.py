@@ -135,11 +135,11 @@ def profiled_fields(summary: str, sources: list):
     return fields
 
 
-def profiled_traffic(summary: str, sources: list, units: int):
-    """DRAM bytes per launch from a committed ncu summary (per-unit figure x units), or
+def profiled_traffic(summary: str, sources: list, units, key: str = "traffic_bytes_per_unit"):
+    """DRAM bytes from a committed ncu summary (the per-unit figure `key` x units), or
     None when the kernel sources changed since the counters were taken."""
     fields = profiled_fields(summary, sources)
-    return None if fields is None else float(fields["traffic_bytes_per_unit"]) * units
+    return None if fields is None or key not in fields else float(fields[key]) * units
 
 
 def profiled_limiter(summary: str, sources: list):
@@ -277,12 +277,17 @@ def run_ours(args, rank, world, local_rank):
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
     torch.cuda.synchronize()
+    # the consumer kernel's own launches, bracketed by CUDA events on the call's stream
+    # inside the library (wdf_explain_timing)
+    wdf.explain_timing(True)
     start.record(stream)
     for k in range(args.steps):
         step(kev[k])
     stop.record(stream)
     torch.cuda.synchronize()
     barrier()
+    kernel_ms_total, kernel_launches = wdf.explain_timing_read()
+    wdf.explain_timing(False)
     launches = wdf.launch_count() - launches0
     clk = clocks.stop()
     ms = start.elapsed_time(stop) / args.steps
@@ -315,6 +320,12 @@ def run_ours(args, rank, world, local_rank):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak_max = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = ops["ops"] * n / (explain_ms * 1e-3) / 1e12
+    # per launch of the consumer kernel alone: its rows (n over the launches of one call)
+    # over its average launch duration
+    launches_per_call = max(1, kernel_launches // max(1, args.steps))
+    rows_per_launch = n / launches_per_call
+    kernel_ms = kernel_ms_total / max(1, kernel_launches)
+    achieved_kernel = ops["ops"] * rows_per_launch / (kernel_ms * 1e-3) / 1e12
     l1 = l1_floor(ens, info["depth"])
     l1_peak = sms * peaks.get("sm_max_mhz", 2070.0) * 1e6
     # background: one compare per inner node and one count per (row, live leaf)
@@ -341,24 +352,37 @@ def run_ours(args, rank, world, local_rank):
         "reduce_ms": ms - explain_ms - background_ms,
         "explain_only_rows_per_s": world * n / (explain_ms * 1e-3),
         "roofline": {
-            "kernel": "the explain call: one k_explain launch (codes, patterns, gathers, phi accumulation)",
+            "kernel": f"k_explain<{info['depth']},64> alone (decisions, entries, gathers, phi accumulation): "
+                      f"{launches_per_call} launches per explain call of {n} rows, {kernel_launches} timed "
+                      "with CUDA events on the call's stream (wdf_explain_timing)",
             "bound": "alu",
-            "achieved": achieved,
+            "achieved": achieved_kernel,
             "peak": alu_peak_max,
             "unit": "Top/s",
-            "frac": achieved / alu_peak_max,
-            "traffic": profiled_traffic("k_explain_large.md", EXPLAIN_SOURCES, n),
+            "frac": achieved_kernel / alu_peak_max,
+            "ms_per_launch": kernel_ms,
+            "rows_per_launch": rows_per_launch,
+            "traffic": profiled_traffic("k_explain_large.md", EXPLAIN_SOURCES, rows_per_launch,
+                                        "kernel_traffic_bytes_per_unit"),
             "limiter_ncu": profiled_limiter("k_explain_large.md", EXPLAIN_SOURCES),
-            "algorithmic_bytes": hbm_bytes,
             "ops_per_row": ops,
             "peak_basis": f"{sms} SMs x 128 lanes/clk x {peaks.get('sm_max_mhz', 2070.0)} MHz (max SM clock, {peak_kind})",
-            "hbm_gbs": hbm_bytes / (explain_ms * 1e-3) / 1e9,
-            "hbm_frac_of_measured": hbm_bytes / (explain_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
             # against the L1 data pipe (the resource ncu shows bounding the kernel): the
             # fewest wavefronts the design needs per row, at one wavefront per SM per clock
             "l1_floor": {**l1, "peak_wavefronts_per_s": l1_peak,
-                         "achieved_floor_wavefronts_per_s": l1["wavefronts_per_row"] * n / (explain_ms * 1e-3),
-                         "frac": l1["wavefronts_per_row"] * n / (explain_ms * 1e-3) / l1_peak},
+                         "achieved_floor_wavefronts_per_s": l1["wavefronts_per_row"] * rows_per_launch / (kernel_ms * 1e-3),
+                         "frac": l1["wavefronts_per_row"] * rows_per_launch / (kernel_ms * 1e-3) / l1_peak},
+            # the whole explain call (the encode kernel and the consumer kernel per chunk)
+            "call": {
+                "achieved": achieved,
+                "frac": achieved / alu_peak_max,
+                "ms": explain_ms,
+                "algorithmic_bytes": hbm_bytes,
+                "traffic": profiled_traffic("k_explain_large.md", EXPLAIN_SOURCES, n),
+                "hbm_gbs": hbm_bytes / (explain_ms * 1e-3) / 1e9,
+                "hbm_frac_of_measured": hbm_bytes / (explain_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                "l1_floor_frac": l1["wavefronts_per_row"] * n / (explain_ms * 1e-3) / l1_peak,
+            },
         },
         "roofline_background": {
             "kernel": "set_background: k_encode_codes (on a side stream, overlapping) + k_bg_hist (patterns, "

@@ -78,7 +78,10 @@ typedef struct {
     int64_t device_bytes;    /* device memory the ensemble holds */
 } wdf_info;
 
-/* Context bound to one CUDA device.  Returns WDF_ECUDA if the device is absent. */
+/* Context bound to one CUDA device.  Returns WDF_ECUDA if the device is absent.
+ * wdf_ctx_destroy releases the caller's handle; the ensembles, batches and servers made
+ * from the context hold it too, so they may be destroyed after it (the context is freed
+ * with the last of them). */
 wdf_status wdf_ctx_create(int32_t device, wdf_ctx **out);
 void wdf_ctx_destroy(wdf_ctx *ctx);
 
@@ -338,6 +341,17 @@ void wdf_debug_contract_wait_limit(int32_t polls);
 /* Number of kernels this library has launched in the process so far (all devices).
  * Benchmarks read it before and after a timed region. */
 int64_t wdf_launch_count(void);
+
+/* Consumer-kernel timing (process-wide; a measurement aid with no counterpart in the
+ * paper).  wdf_explain_timing(1) makes every later wdf_explain bracket each launch of
+ * its consumer kernel (Algorithm 3 step 4, one launch per 2^20 rows) with a pair of CUDA
+ * events on the call's stream; wdf_explain_timing(0) stops; either call forgets the
+ * pairs recorded so far.  wdf_explain_timing_read waits for the recorded pairs, writes
+ * their summed milliseconds and their count (the launches timed), and forgets them.
+ * Reading while another thread is inside wdf_explain returns only the pairs that call
+ * has finished recording.  WDF_EINVAL for null outputs, WDF_ECUDA if an event fails. */
+wdf_status wdf_explain_timing(int32_t enable);
+wdf_status wdf_explain_timing_read(double *ms, int64_t *launches);
 
 const char *wdf_last_error(void);
 const char *wdf_version(void);

@@ -19,7 +19,7 @@ _BINDING_NAMES = (
     "background_counts", "background_counts_size",
     "batch_autotune", "batch_create", "batch_explain", "batch_tile_rows",
     "ctx_create", "debug_contract_wait_limit", "debug_leaf_hist", "debug_pair_table",
-    "ensemble_info", "expected_value", "explain", "explain_interactions",
+    "ensemble_info", "expected_value", "explain", "explain_interactions", "explain_timing", "explain_timing_read",
     "global_attribution", "global_attribution_noalloc",
     "launch_count", "library_path", "load_ensemble",
     "server_create", "server_poll", "server_request_ms", "server_reset_stats", "server_stats", "server_submit", "server_wait",

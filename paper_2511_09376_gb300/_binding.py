@@ -61,6 +61,8 @@ _lib.wdf_ensemble_destroy.argtypes = [_vp]
 _lib.wdf_ensemble_destroy.restype = None
 _lib.wdf_batch_destroy.argtypes = [_vp]
 _lib.wdf_batch_destroy.restype = None
+_lib.wdf_explain_timing.argtypes = [_c.c_int32]
+_lib.wdf_explain_timing_read.argtypes = [_c.POINTER(_c.c_double), _c.POINTER(_c.c_int64)]
 _lib.wdf_debug_contract_wait_limit.argtypes = [_c.c_int32]
 _lib.wdf_debug_contract_wait_limit.restype = None
 
@@ -89,6 +91,20 @@ def library_path() -> str:
 def launch_count() -> int:
     """Kernels the library has launched in this process."""
     return int(_lib.wdf_launch_count())
+
+
+def explain_timing(enable: bool) -> None:
+    """Bracket every later consumer-kernel launch of wdf_explain with CUDA events (True)
+    or stop (False); either forgets the launches timed so far."""
+    _check(_lib.wdf_explain_timing(1 if enable else 0))
+
+
+def explain_timing_read():
+    """(summed milliseconds, launches) of the consumer-kernel launches timed since the
+    last read; waits for them."""
+    ms, n = _c.c_double(0.0), _c.c_int64(0)
+    _check(_lib.wdf_explain_timing_read(_c.byref(ms), _c.byref(n)))
+    return float(ms.value), int(n.value)
 
 
 def version() -> str:

@@ -296,6 +296,18 @@ void wdf_debug_contract_wait_limit(int32_t polls) { wdf::set_contract_first_wait
 
 int64_t wdf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+wdf_status wdf_explain_timing(int32_t enable) {
+    wdf::explain_timing(enable != 0);
+    return WDF_OK;
+}
+
+wdf_status wdf_explain_timing_read(double *ms, int64_t *launches) {
+    if (!ms || !launches) return fail(WDF_EINVAL, "null output");
+    const cudaError_t e = wdf::explain_timing_read(ms, launches);
+    if (e != cudaSuccess) return cuda_fail(e, "wdf_explain_timing_read");
+    return WDF_OK;
+}
+
 wdf_status wdf_ctx_create(int32_t device, wdf_ctx **out) {
     if (!out) return fail(WDF_EINVAL, "out is null");
     *out = nullptr;
@@ -319,7 +331,7 @@ wdf_status wdf_ctx_create(int32_t device, wdf_ctx **out) {
     return WDF_OK;
 }
 
-void wdf_ctx_destroy(wdf_ctx *ctx) { delete ctx; }
+void wdf_ctx_destroy(wdf_ctx *ctx) { ctx_release(ctx); }
 
 wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, const int64_t *tree_offset,
                              const int32_t *feature, const float *threshold, const int32_t *left,
@@ -328,12 +340,13 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
     if (!ctx || !out) return fail(WDF_EINVAL, "ctx and out must be non-null");
     *out = nullptr;
     wdf_ensemble *e = new wdf_ensemble();
-    e->ctx = ctx;
+    e->ctx = ctx_retain(ctx);
     std::string err;
     const int rc = wdf::pack_ensemble(n_features, n_trees, tree_offset, feature, threshold, left, right, value,
                                       &e->pk, &err);
     if (rc != 0) {
         delete e;
+        ctx_release(ctx);
         return fail((wdf_status)rc, err);
     }
     DeviceGuard g(ctx->device);
@@ -393,6 +406,7 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
     if (ce != cudaSuccess) {
         free_ensemble(e);
         delete e;
+        ctx_release(ctx);
         return cuda_fail(ce, "wdf_load_ensemble");
     }
     *out = e;
@@ -401,10 +415,14 @@ wdf_status wdf_load_ensemble(wdf_ctx *ctx, int32_t n_features, int32_t n_trees, 
 
 void wdf_ensemble_destroy(wdf_ensemble *ens) {
     if (!ens) return;
-    DeviceGuard g(ens->ctx->device);
-    cudaDeviceSynchronize();
-    free_ensemble(ens);
-    delete ens;
+    wdf_ctx *ctx = ens->ctx;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        free_ensemble(ens);
+        delete ens;
+    }
+    ctx_release(ctx);
 }
 
 wdf_status wdf_ensemble_info(const wdf_ensemble *ens, wdf_info *out) {

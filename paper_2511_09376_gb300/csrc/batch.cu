@@ -274,7 +274,7 @@ wdf_status wdf_batch_create(wdf_ctx *ctx, int32_t n_ensembles, wdf_ensemble *con
     cudaGetDevice(&prev);
     if (prev != ctx->device) cudaSetDevice(ctx->device);
     wdf_batch *b = new wdf_batch();
-    b->ctx = ctx;
+    b->ctx = ctx_retain(ctx);
     b->ens.assign(ensembles, ensembles + n_ensembles);
     b->cls_of.assign((size_t)n_ensembles, -1);
     b->slot_of.assign((size_t)n_ensembles, -1);
@@ -337,6 +337,7 @@ void wdf_batch_destroy(wdf_batch *b) {
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_copied) cudaEventDestroy(b->ev_copied);
     if (b->ctx && prev >= 0 && prev != b->ctx->device) cudaSetDevice(prev);
+    ctx_release(b->ctx);
     delete b;
 }
 

@@ -1,10 +1,49 @@
 // Depth and tile dispatch of the consumer kernels (k_explain.cuh); the kernels are
 // compiled in the k_explain_d*.cu translation units.
 #include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "k_explain.cuh"
 
 namespace wdf {
+
+namespace {
+std::mutex g_tmu;
+bool g_timing = false;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_tev;
+
+void drop_events() {
+    for (auto &p : g_tev) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    g_tev.clear();
+}
+}  // namespace
+
+void explain_timing(bool on) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    drop_events();
+    g_timing = on;
+}
+
+cudaError_t explain_timing_read(double *ms, int64_t *launches) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    double total = 0.0;
+    cudaError_t err = cudaSuccess;
+    for (auto &p : g_tev) {
+        float t = 0.0f;
+        if (err == cudaSuccess) err = cudaEventSynchronize(p.second);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&t, p.first, p.second);
+        total += t;
+    }
+    *ms = total;
+    *launches = (int64_t)g_tev.size();
+    drop_events();
+    return err;
+}
 
 WDF_EXPLAIN_DEPTH(2, extern)
 WDF_EXPLAIN_DEPTH(3, extern)
@@ -60,6 +99,18 @@ cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const 
         err = launch_encode_codes(C + r0 * ldc, rows, ldc, job.ta, (rows + pad - 1) / pad * pad, codes, st);
         if (err != cudaSuccess) break;
         float *out = phi + r0 * ldp;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_tmu);
+            if (g_timing && cudaEventCreate(&ev0) == cudaSuccess) {
+                if (cudaEventCreate(&ev1) == cudaSuccess) {
+                    cudaEventRecord(ev0, st);
+                } else {
+                    cudaEventDestroy(ev0);
+                    ev0 = ev1 = nullptr;
+                }
+            }
+        }
         switch (D) {
             case 2: err = explain_depth<2>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
             case 3: err = explain_depth<3>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
@@ -68,6 +119,11 @@ cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const 
             case 6: err = explain_depth<6>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
             case 7: err = explain_depth<7>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
             default: err = explain_depth<8>(codes, rows, job, out, ldp, tile_rows, dev, st); break;
+        }
+        if (ev1) {  // the pair is kept only once both ends are recorded
+            std::lock_guard<std::mutex> lk(g_tmu);
+            cudaEventRecord(ev1, st);
+            g_tev.emplace_back(ev0, ev1);
         }
     }
     const cudaError_t ferr = cudaFreeAsync(codes, st);

@@ -152,6 +152,12 @@ cudaError_t launch_base_value(int D, const uint32_t *vc, const double *ratio, co
 // 0 picks the default for the shared-memory budget).
 cudaError_t launch_explain(int D, const float *C, int64_t n, int64_t ldc, const ExplainJob &job, float *phi,
                            int64_t ldp, int tile_rows, const DevInfo &dev, cudaStream_t st);
+// Consumer-kernel timing (process-wide): while on, launch_explain brackets every
+// consumer-kernel launch with a pair of CUDA events on its stream; explain_timing_read
+// waits for the recorded pairs, returns the summed milliseconds and the launch count, and
+// forgets them.  Turning it on or off also forgets them.
+void explain_timing(bool on);
+cudaError_t explain_timing_read(double *ms, int64_t *launches);
 // xb: decision-code bytes per row (code columns x code bytes).
 int default_tile_rows(int D, int F, int xb, const DevInfo &dev);
 size_t explain_smem_bytes(int D, int F, int xb, int tile_rows);

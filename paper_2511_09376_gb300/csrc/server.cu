@@ -342,7 +342,7 @@ wdf_status wdf_server_create(wdf_ctx *ctx, int32_t n_ensembles, wdf_ensemble *co
     cudaGetDevice(&prev);
     if (prev != ctx->device) cudaSetDevice(ctx->device);
     wdf_server *s = new wdf_server();
-    s->ctx = ctx;
+    s->ctx = ctx_retain(ctx);
     s->ens.assign(ensembles, ensembles + n_ensembles);
     s->budget = device_budget_bytes;
     s->n_slots = n_slots;
@@ -367,6 +367,7 @@ wdf_status wdf_server_create(wdf_ctx *ctx, int32_t n_ensembles, wdf_ensemble *co
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     if (st != WDF_OK) {
         for (wdf_batch *b : s->batch) wdf_batch_destroy(b);
+        ctx_release(s->ctx);
         delete s;
         return st;
     }
@@ -486,6 +487,7 @@ void wdf_server_destroy(wdf_server *s) {
     }
     for (wdf_batch *b : s->batch) wdf_batch_destroy(b);
     if (prev >= 0 && prev != s->ctx->device) cudaSetDevice(prev);
+    ctx_release(s->ctx);
     delete s;
 }
 

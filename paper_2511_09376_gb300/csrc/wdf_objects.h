@@ -1,5 +1,6 @@
 // Library object definitions shared by the C-ABI translation units (internal).
 #pragma once
+#include <atomic>
 #include <cstdint>
 
 #include "launch.h"
@@ -8,7 +9,17 @@
 struct wdf_ctx {
     int device = 0;
     wdf::DevInfo dev;
+    // the caller's handle plus one reference per ensemble, batch and server made from the
+    // context, so wdf_ctx_destroy may come before theirs: the last reference frees it
+    std::atomic<int> refs{1};
 };
+inline wdf_ctx *ctx_retain(wdf_ctx *c) {
+    c->refs.fetch_add(1, std::memory_order_relaxed);
+    return c;
+}
+inline void ctx_release(wdf_ctx *c) {
+    if (c && c->refs.fetch_sub(1, std::memory_order_acq_rel) == 1) delete c;
+}
 
 struct wdf_ensemble {
     wdf_ctx *ctx = nullptr;
