@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(RT) k_bg_hist(const unsigned char *__restrict_
 // Tree chunking of one launch: G trees per block with counters in shared memory whenever
 // one tree's counters fit beside the code tile; otherwise the counts go straight to
 // global memory and only the node records are chunked.  Deep trees (64 KB of counters
-// per depth-8 tree) then take one or two trees per block and hundreds of chunks, each
+// per depth-8 tree) then take one to a few trees per block and hundreds of chunks, each
 // block streaming every code tile through shared memory (from L2, where the blocks
 // walking the same tiles meet): 47.5 instead of 62.8 ms per 1M rows for 500 trees of
 // depth 7, 203 instead of 254 ms for 1000 of depth 8, against global-memory atomics.
